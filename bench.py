@@ -1,0 +1,363 @@
+"""Benchmark: KMC events/s of the fractional-step sweep on one GB300.
+
+Workload (default): the 2D Ising spin-flip Arrhenius benchmark of Section 7
+on a 1024x1024 periodic lattice at betaJ = 0.4407, 16x16 cells, Lie
+splitting with dt = 1, binary64 window clocks. One step = 10 units of
+physical time (20 fractional windows) plus the observables (coverage,
+energy, pair correlations up to r = 32): every stage of the hot path.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on
+a bounded sample of the same workload instead. Under torchrun each rank runs
+its own independent lattice (replicas only: the path needs no collective);
+the barrier and the max-over-ranks timing use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import WORKLOADS  # noqa: E402
+
+METRIC = "KMC events/sec on 1 GB300 (batched FP32-clock vs plain FP64) at stated Δt-error"
+STEP_T = 10.0
+RMAX = 32
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="ising1024")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-variants", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# Algorithmic work of one event of the spin-flip models on the warp-per-cell
+# design (lane-operations, integer or floating point): one Philox4x32-10
+# block (10 rounds x 8 ops + 9 key bumps x 2), the waiting time (1 log + 1
+# divide, ~30), the class threshold chain (2 ops x 10 classes), the rank
+# search over 32 lanes (popcount + 5-step scan + ballot/select, ~12 ops per
+# lane) and the class refresh of the 5 sites a flip touches (~15 ops each).
+OPS_PER_EVENT = 98 + 30 + 20 + 12 * 32 + 5 * 15
+
+
+def cpu_baseline(w, seconds):
+    """The oracle as it stands on a bounded sample of the workload: a 256x256
+    lattice of the same model, rates, cell shape and schedule, advanced step
+    by step until `seconds` of CPU time. Events/s do not depend on the
+    lattice size for the cell-by-cell oracle (cost per event ~ cell size)."""
+    import oracle
+    lx = ly = 256
+    run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
+                       oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
+    t0 = time.process_time()
+    steps = 0
+    while time.process_time() - t0 < seconds:
+        run.run(w["scheme"], w["dt"], w["dt"], w["seed"])
+        steps += 1
+    dt = time.process_time() - t0
+    return {"value": run.events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"256x256 lattice, same model/rates/cells/schedule, {steps} Lie steps "
+                      f"of dt={w['dt']} ({run.events} events, {dt:.1f} s CPU, single thread)"}
+
+
+def run_reference(args, rank, world):
+    w = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    cb = None
+    vals = []
+    import oracle
+    lx = ly = 256
+    run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
+                       oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
+    for i in range(args.warmup + args.steps):
+        e0 = run.events
+        t0 = time.perf_counter()
+        run.run(w["scheme"], w["dt"], w["dt"], w["seed"])
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            vals.append(((run.events - e0), t1 - t0))
+    ev = sum(v[0] for v in vals)
+    tt = sum(v[1] for v in vals)
+    value = ev / tt
+    cb = {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+          "sample": f"256x256 lattice of the {args.workload} workload, one Lie step of dt="
+                    f"{w['dt']} per bench step, single thread"}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tt / max(len(vals), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " (256x256 sample on the host CPU)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    from paper_1105_4673_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS[args.workload]
+    lx, ly = w["lx"], w["ly"]
+    seed = w["seed"] + 7919 * rank
+    ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream)
+    ctx.init_random(seed, w.get("coverage", 0.5))
+    col, hh = schedule(w, STEP_T)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step(kernel_events=None):
+        for c, h in zip(col, hh):
+            if kernel_events is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.window(int(c), float(h), seed)
+                b.record(stream)
+                kernel_events.append((a, b))
+            else:
+                ctx.window(int(c), float(h), seed)
+        return ctx.observables(0, RMAX)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = ctx.stats()["events"]
+    barrier(world)
+    torch.cuda.synchronize()
+    kev = []
+    step_times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the step's events)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            step(kev)
+            s1.record(stream)
+            step_times.append((s0, s1))
+        torch.cuda.synchronize()
+    barrier(world)
+    events = ctx.stats()["events"] - ev0
+    t_ms = sum(a.elapsed_time(b) for a, b in step_times)
+    t_ms = max_over_ranks(t_ms, world)
+    events_all = sum_over_ranks(events, world)
+    kernel_ms = [a.elapsed_time(b) for a, b in kev]
+    value = events_all / (t_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: H2D of the state from
+    # pinned memory, the step, D2H of the state and the observables
+    host = torch.empty(lx * ly, dtype=torch.uint8, pin_memory=True)
+    hnp = host.numpy()
+    ctx.get_state(0, hnp)
+    torch.cuda.synchronize()
+    e_ev0 = ctx.stats()["events"]
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state(hnp)
+        ctx.run(w["scheme"], w["dt"], STEP_T, seed)
+        ctx.observables(0, RMAX)
+        ctx.get_state(0, hnp)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_events = sum_over_ranks(ctx.stats()["events"] - e_ev0, world)
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        variants = measure_variants(F, w, stream, seed, steps=max(2, args.steps // 2))
+
+    if rank != 0:
+        ctx.close()
+        return
+    pk = peaks()
+    cs = clk.summary()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # Gop/s, INT32/FP32 lanes at max clock
+    k_events_per_launch = events / max(len(kernel_ms), 1)
+    k_avg_s = float(np.mean(kernel_ms)) / 1000.0
+    achieved = k_events_per_launch * OPS_PER_EVENT / k_avg_s / 1e9
+    cb = cpu_baseline(w, args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {lx}x{ly} {w['model']} betaJ="
+                               f"{w['rates'].get('betaJ')} q={w['q'][0]} {w['scheme']} dt={w['dt']}",
+                   "step": f"{STEP_T:g} time units ({len(col)} windows) + observables",
+                   "clock": "fp64", "engine": "plain", "l2": "flushed between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "fs_window_kernel<ISING,double>",
+                     "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
+                     "ops_per_event": OPS_PER_EVENT,
+                     "peak_note": "152 SMs x 128 INT32/FP32 lanes x max SM clock (derived)"},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
+                "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
+        "gpu_launches": len(kernel_ms) + args.steps,
+        "clocks": cs,
+        "variants": variants,
+    }
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def measure_variants(F, w, stream, seed, steps):
+    """The same workload through the persistent engine (one graph-launched
+    kernel per run) with binary64 and binary32 window clocks."""
+    import torch
+    res = {}
+    for engine, clock in (("PERSISTENT", "FP64"), ("PERSISTENT", "FP32"), ("PLAIN", "FP32")):
+        c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream)
+        c.set_engine(engine)
+        c.set_clock(clock)
+        c.init_random(seed, w.get("coverage", 0.5))
+        c.run(w["scheme"], w["dt"], STEP_T, seed)
+        torch.cuda.synchronize()
+        e0 = c.stats()["events"]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            c.run(w["scheme"], w["dt"], STEP_T, seed)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ev = c.stats()["events"] - e0
+        res[f"{engine.lower()}_{clock.lower()}"] = {"events_per_s": ev / (a.elapsed_time(b) / 1000),
+                                                    "events": ev}
+        c.close()
+    return res
+
+
+def schedule(w, T):
+    # the window sequence of one step (fixed schedules only)
+    if w["scheme"] == "LIE":
+        n = int(round(T / w["dt"]))
+        return [0, 1] * n, [w["dt"]] * (2 * n)
+    if w["scheme"] == "STRANG":
+        n = int(round(T / w["dt"]))
+        return [0, 1, 0] * n, [w["dt"] / 2, w["dt"], w["dt"] / 2] * n
+    raise ValueError("bench steps use a deterministic schedule")
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+if __name__ == "__main__":
+    main()

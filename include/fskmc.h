@@ -1,0 +1,235 @@
+/*
+ * fskmc.h -- C ABI of the GB300 fractional-step parallel kinetic Monte Carlo
+ * library (Arampatzis, Katsoulakis, Plechac, Taufer, Xu, "Hierarchical
+ * fractional-step approximations and parallel kinetic Monte Carlo
+ * algorithms", arXiv:1105.4673).
+ *
+ * The lattice is split into a checkerboard of coarse cells (Section 2.1,
+ * Eq. sublatt). In each fractional window every cell of the active colour
+ * runs its own serial SSA (Eqs. totalrate and skeleton) for the window length,
+ * reading its neighbours' sites as they were when the window began (Section
+ * 2.2, Steps 1-3). The colours are composed by Lie (Eq. lie), Strang
+ * (Eq. strang) or random (Eq. SLPCS) schedules (Section 3).
+ *
+ * General rules for every call:
+ *  - Calls return a status code; nothing is thrown or aborted across the
+ *    ABI. On failure fskmc_last_error() describes the cause.
+ *  - A context is used by one host thread at a time.
+ *  - The library owns all device memory of a context. Pointers passed in are
+ *    borrowed for the duration of the call only.
+ *  - Work is queued on the context's CUDA stream (given at creation; NULL
+ *    means the legacy default stream). Calls that return data to the host
+ *    (fskmc_get_state to host memory, fskmc_observables, fskmc_stats,
+ *    fskmc_workload, fskmc_sync) wait for the stream.
+ *  - Lattices are periodic lx*ly, one byte per site, row-major: site (x,y)
+ *    is byte y*lx+x. Binary models use 0/1 (1 = occupied, or spin +1 for
+ *    ISING); ZGB uses 0 empty, 1 A, 2 B.
+ *  - Random numbers are Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *    seed, counter (event, window, cell, replica | tag<<24); results depend
+ *    on the seed, the window index, the cell shape and the clock precision,
+ *    never on launch configuration.
+ */
+#ifndef FSKMC_H
+#define FSKMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fskmc_ctx fskmc_ctx;
+
+typedef enum {
+    FSKMC_OK = 0,
+    FSKMC_EINVAL = 1,   /* invalid argument (sizes, rates, schedule, pointers) */
+    FSKMC_ENOMEM = 2,   /* device or host allocation failed */
+    FSKMC_ECUDA = 3,    /* a CUDA call failed (message in fskmc_last_error) */
+    FSKMC_ETIMEOUT = 4, /* a bounded device wait gave up (persistent engine) */
+    FSKMC_ESTATE = 5    /* call not valid in the context's current state */
+} fskmc_status;
+
+/* Models (Section 2 examples; rates in fskmc_rates). */
+typedef enum {
+    /* adsorption/desorption spin flip, Eq. adsdesrate with nearest-neighbour
+       J: r(empty) = ka, r(occupied, n) = kd exp(-betaJ n) */
+    FSKMC_ADSDES = 0,
+    /* Ising spin-flip Arrhenius dynamics, Eq. Arrhenius at zero spin field
+       (U = K n - h, K = 4J, h = 2K): r(0) = ka, r(1, n) = kd exp(-4 betaJ (n-2)) */
+    FSKMC_ISING_ARRHENIUS = 1,
+    /* ADSDES plus nearest-neighbour hops (Section 2 example 2) of a particle
+       with n occupied neighbours onto an empty site: nu exp(-betaJ n) */
+    FSKMC_ADSDES_DIFFUSION = 2,
+    /* ZGB CO-oxidation (Table COrates): A adsorbs (yA), B2 adsorbs on an
+       empty pair ((1-yA)/4 per directed pair), A+B react ((kr/4) per
+       directed pair), A desorbs (kd) */
+    FSKMC_ZGB = 3
+} fskmc_model;
+
+/* Processor communication schedules (Section 3). */
+typedef enum {
+    FSKMC_LIE = 0,         /* E(dt) O(dt) per step, Eq. lie */
+    FSKMC_STRANG = 1,      /* E(dt/2) O(dt) E(dt/2) per step, Eq. strang */
+    FSKMC_RANDOM = 2,      /* sub-lattice random schedule, Eq. SLPCS: 2T/dt windows of
+                              length dt, colour fair per window */
+    FSKMC_RANDOM_ORDER = 3 /* per step (E,O) or (O,E) with probability 1/2, each dt */
+} fskmc_scheme;
+
+/* Precision of the per-cell window clock. FP64: lambda, waiting times and
+   the class thresholds in binary64, results bit-identical to the CPU
+   oracle. FP32: the same integer class counts and member selection, but
+   lambda, waiting times and thresholds in binary32 relative to the window
+   start (statistically equivalent, not bit-identical). */
+typedef enum { FSKMC_CLOCK_FP64 = 0, FSKMC_CLOCK_FP32 = 1 } fskmc_clock;
+
+/* PLAIN: one kernel launch per window (per replica). PERSISTENT: one
+   launch runs every window of every replica, cells advancing as soon as
+   their neighbours have finished the previous window; launched through a
+   CUDA graph. */
+typedef enum { FSKMC_ENGINE_PLAIN = 0, FSKMC_ENGINE_PERSISTENT = 1 } fskmc_engine;
+
+typedef struct {
+    int32_t lx, ly;    /* lattice sides; lx % (2 qx) == 0 and ly % (2 qy) == 0 */
+    int32_t bitpacked; /* reserved, must be 0 */
+} fskmc_lattice;
+
+typedef struct {
+    double ka, kd, betaJ, nu, yA, kr; /* fields a model does not use are ignored */
+} fskmc_rates;
+
+typedef struct {
+    int32_t qx, qy; /* coarse cell shape, 1..32 each with qx*qy <= 1024;
+                       {0,0} asks the autotuner to pick a square q in {8,16,32} */
+} fskmc_cell_shape;
+
+/*
+ * Create a single-lattice context (Section 2.1: lattice, decomposition into
+ * qx*qy cells, model rates). The lattice starts empty (all 0).
+ * EINVAL: lx or ly not a positive multiple of 2q; q out of range; models
+ * with two-site events and q < 2; ADSDES_DIFFUSION with lx < qx+4 or
+ * ly < qy+4 (its frozen halo is two sites wide); negative or non-finite
+ * rates; yA outside [0,1]; out == NULL.
+ * stream: a cudaStream_t (or NULL); the context keeps it, not owns it.
+ */
+fskmc_status fskmc_create(const fskmc_lattice *lattice, fskmc_model model,
+                          const fskmc_rates *rates, fskmc_cell_shape cell,
+                          void *stream, fskmc_ctx **out);
+
+/*
+ * Create a context holding n independent replicas (the paper's M
+ * independent realisations, Section 7) of possibly different sizes and
+ * rates, all of the same model and cell shape. Replica r uses r as the
+ * replica word of every random counter, so replica r of a batch evolves
+ * exactly like a single context whose replica id is r
+ * (fskmc_set_replica_id). lattices[n], rates[n]. Same EINVAL rules as
+ * fskmc_create, for every replica; also n < 1 or n > 65536.
+ */
+fskmc_status fskmc_batch_create(int32_t n, const fskmc_lattice *lattices,
+                                fskmc_model model, const fskmc_rates *rates,
+                                fskmc_cell_shape cell, void *stream, fskmc_ctx **out);
+
+/* Free every resource of the context (waits for its stream). NULL is a no-op. */
+void fskmc_destroy(fskmc_ctx *ctx);
+
+/* Last error message of the context (never NULL; "" after success). With
+   ctx == NULL: the last error of a failed create call on this thread. */
+const char *fskmc_last_error(const fskmc_ctx *ctx);
+
+/* Replica id of a single context (default 0); EINVAL for batches or id >= 2^24. */
+fskmc_status fskmc_set_replica_id(fskmc_ctx *ctx, uint32_t id);
+
+fskmc_status fskmc_set_clock(fskmc_ctx *ctx, fskmc_clock clock);
+fskmc_status fskmc_set_engine(fskmc_ctx *ctx, fskmc_engine engine);
+
+/* Launch shape of the window kernels: warps (= cells) per block, 1..16.
+   Results do not depend on it. */
+fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
+
+/* Persistent engine: how many times a cell polls a neighbour's progress
+   before giving up (default 2^24, about a second or more). A run whose wait
+   gives up returns FSKMC_ETIMEOUT and leaves the lattice undefined. */
+fskmc_status fskmc_set_spin_limit(fskmc_ctx *ctx, uint32_t polls);
+
+/* Effective cell shape and sizes: out[0]=qx, out[1]=qy, out[2]=replicas,
+   out[3]=total cells over replicas, out[4]=warps per block. */
+fskmc_status fskmc_info(const fskmc_ctx *ctx, int32_t out[5]);
+
+/*
+ * Bernoulli(coverage) initial state of every replica: site i of replica r
+ * is 1 iff word 0 of Philox(seed, (i, 0, 0, r | 2<<24)) < coverage * 2^32.
+ * EINVAL: coverage outside [0,1].
+ */
+fskmc_status fskmc_init_random(fskmc_ctx *ctx, uint64_t seed, double coverage);
+
+/*
+ * Gaussian-bump pre-coverage: site (x,y) holds `species` with probability
+ * amp * g(dx) * g(dy), g(d) = exp(-d^2 / (2 width^2)), d the periodic
+ * distance to a centre drawn from Philox(seed, (0, 0xFFFFFFFF, 0, r|3<<24))
+ * (x0 = word0 mod lx, y0 = word1 mod ly); empty otherwise (same per-site
+ * draw as fskmc_init_random). EINVAL: amp outside [0,1], width <= 0,
+ * species not a state of the model.
+ */
+fskmc_status fskmc_init_bump(fskmc_ctx *ctx, uint64_t seed, double amp, double width,
+                             int32_t species);
+
+/* Copy a replica's lattice in (lx*ly bytes, row-major). is_device != 0: src
+   is device memory (read on the context's stream). EINVAL: replica out of
+   range, NULL src, a byte that is not a state of the model. */
+fskmc_status fskmc_set_state(fskmc_ctx *ctx, int32_t replica, const uint8_t *src,
+                             int32_t is_device);
+
+/* Copy a replica's lattice out (lx*ly bytes). is_device != 0: dst is device
+   memory (written on the stream, not waited for). */
+fskmc_status fskmc_get_state(fskmc_ctx *ctx, int32_t replica, uint8_t *dst,
+                             int32_t is_device);
+
+/*
+ * Advance every replica by physical time T with fractional windows of
+ * length dt under the given schedule (Section 3). The window counter
+ * continues across calls, so two runs of T/2 equal one run of T. T/dt must
+ * be an integer within 1e-9 relative (EINVAL otherwise, or dt <= 0, T < 0).
+ * Asynchronous on the context's stream. ETIMEOUT (persistent engine only):
+ * a cell waited too long for a neighbour; the lattice is then undefined.
+ */
+fskmc_status fskmc_run(fskmc_ctx *ctx, fskmc_scheme scheme, double dt, double T,
+                       uint64_t seed);
+
+/* One window of colour (0 = E, 1 = O) and length h at the current window
+   index (then incremented), for every replica. EINVAL: h <= 0, colour not 0/1. */
+fskmc_status fskmc_window(fskmc_ctx *ctx, int32_t colour, double h, uint64_t seed);
+
+/* Current global window index, and setting it (for resume). */
+fskmc_status fskmc_get_window_index(const fskmc_ctx *ctx, uint64_t *w);
+fskmc_status fskmc_set_window_index(fskmc_ctx *ctx, uint64_t w);
+
+/*
+ * Observables of Section 7 for one replica, from exact integer sums:
+ * coverage[3] = fraction of sites in state 0, 1, 2; energy = -(occupied
+ * nearest-neighbour pairs)/N for ADSDES and ADSDES_DIFFUSION,
+ * -(1/N) sum_<xy> s_x s_y with s = 2 sigma - 1 for ISING, NaN for ZGB;
+ * paircorr[2*rmax] = G_x(1..rmax) then G_y(1..rmax), G_e(r) = (1/N) sum_x
+ * [sigma(x)=1][sigma(x + r e)=1]. paircorr may be NULL when rmax == 0.
+ * EINVAL: rmax < 0 or rmax > min(lx, ly), NULL coverage/energy.
+ */
+fskmc_status fskmc_observables(fskmc_ctx *ctx, int32_t replica, double *coverage,
+                               double *energy, double *paircorr, int32_t rmax);
+
+/* Counters since creation: out[0] events executed, out[1] windows run,
+   out[2] cell-windows whose last waiting time landed within 1e-12
+   (relative) of the window edge, out[3] bounded waits that gave up,
+   out[4] cell-windows stopped by the kernel's internal consistency check
+   (class counts disagreeing with the member masks; always 0 unless the
+   library is broken). */
+fskmc_status fskmc_stats(fskmc_ctx *ctx, uint64_t out[5]);
+
+/* Workload W(m) of Eq. wload: events each cell of a replica executed in its
+   most recent window, out[ncx*ncy], cell id m = cy*ncx + cx. */
+fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);
+
+/* Wait until all work queued on the context's stream has finished. */
+fskmc_status fskmc_sync(fskmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSKMC_H */

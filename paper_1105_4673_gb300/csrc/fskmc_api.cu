@@ -1,0 +1,649 @@
+// Host side of the C ABI declared in include/fskmc.h: contexts, argument
+// validation, class-rate tables, processor communication schedules and the
+// plain (one launch per window) engine.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fskmc.h"
+#include "fskmc_internal.h"
+#include "fskmc_persistent.h"
+#include "philox.cuh"
+
+using fskmc::Replica;
+
+struct fskmc_ctx {
+    int model = 0, nclass = 0, nstates = 2;
+    int nrep = 0;
+    int qx = 0, qy = 0;
+    bool batch = false;
+    std::vector<Replica> reps;
+    Replica *d_reps = nullptr;
+    uint8_t *d_lat[2] = {nullptr, nullptr};  // [1] only for the ping-pong model
+    int cur = 0;                             // which buffer holds the state
+    int64_t total_sites = 0;
+    int32_t total_cells = 0;
+    int32_t *d_workload = nullptr;
+    unsigned long long *d_counters = nullptr;  // events, ambiguous, timeouts, spare
+    unsigned int *d_scratch_u32 = nullptr;
+    unsigned long long *d_obs = nullptr;
+    int obs_cap = 0;
+    uint64_t w = 0;        // global window index
+    uint64_t windows = 0;  // windows run
+    fskmc_clock clock = FSKMC_CLOCK_FP64;
+    fskmc_engine engine = FSKMC_ENGINE_PLAIN;
+    int wpb = 4;
+    uint32_t spin_limit = 1u << 24;
+    cudaStream_t stream = nullptr;
+    fskmc::PersistentState *pers = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+fskmc_status fail(fskmc_ctx *c, fskmc_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return st;
+}
+
+#define CK(ctx, call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail((ctx), FSKMC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+// Class rates in class order; the same formulas and the same order of
+// floating-point operations as the model definitions in include/fskmc.h.
+int class_rates(int model, const fskmc_rates &q, double *r)
+{
+    switch (model) {
+    case fskmc::ADSDES:
+        for (int n = 0; n < 5; ++n) {
+            r[n] = q.ka;
+            r[5 + n] = q.kd * std::exp(-(q.betaJ * (double)n));
+        }
+        return 10;
+    case fskmc::ISING:
+        for (int n = 0; n < 5; ++n) {
+            r[n] = q.ka;
+            r[5 + n] = q.kd * std::exp(-(4.0 * q.betaJ) * (double)(n - 2));
+        }
+        return 10;
+    case fskmc::DIFFUSION:
+        for (int n = 0; n < 5; ++n) {
+            r[n] = q.ka;
+            r[5 + n] = q.kd * std::exp(-(q.betaJ * (double)n));
+            r[10 + n] = q.nu * std::exp(-(q.betaJ * (double)n));
+        }
+        return 15;
+    case fskmc::ZGB:
+        r[0] = q.yA;
+        r[1] = (1.0 - q.yA) * 0.25;
+        r[2] = q.kr * 0.25;
+        r[3] = q.kd;
+        return 4;
+    }
+    return -1;
+}
+
+fskmc_status check_rates(int model, const fskmc_rates &q)
+{
+    switch (model) {
+    case fskmc::ADSDES:
+    case fskmc::ISING:
+        if (!finite_nonneg(q.ka) || !finite_nonneg(q.kd) || !std::isfinite(q.betaJ))
+            return fail(nullptr, FSKMC_EINVAL, "rates: ka, kd must be finite and >= 0, betaJ finite");
+        break;
+    case fskmc::DIFFUSION:
+        if (!finite_nonneg(q.ka) || !finite_nonneg(q.kd) || !finite_nonneg(q.nu) ||
+            !std::isfinite(q.betaJ))
+            return fail(nullptr, FSKMC_EINVAL, "rates: ka, kd, nu must be finite and >= 0, betaJ finite");
+        break;
+    case fskmc::ZGB:
+        if (!(q.yA >= 0.0 && q.yA <= 1.0) || !finite_nonneg(q.kr) || !finite_nonneg(q.kd))
+            return fail(nullptr, FSKMC_EINVAL, "rates: yA must be in [0,1], kr and kd finite and >= 0");
+        break;
+    default:
+        return fail(nullptr, FSKMC_EINVAL, "unknown model %d", model);
+    }
+    double r[16];
+    int nc = class_rates(model, q, r);
+    for (int k = 0; k < nc; ++k)
+        if (!std::isfinite(r[k]) || r[k] < 0.0 || (float)r[k] == INFINITY)
+            return fail(nullptr, FSKMC_EINVAL, "rate of class %d is not finite (%g)", k, r[k]);
+    return FSKMC_OK;
+}
+
+fskmc_status check_geometry(int model, const fskmc_lattice &L, int qx, int qy)
+{
+    if (L.bitpacked != 0) return fail(nullptr, FSKMC_EINVAL, "bitpacked lattices are not supported");
+    if (qx < 1 || qy < 1 || qx > fskmc::MAX_Q || qy > fskmc::MAX_Q)
+        return fail(nullptr, FSKMC_EINVAL, "cell shape %dx%d out of range 1..32", qx, qy);
+    if (L.lx < 2 * qx || L.ly < 2 * qy || L.lx % (2 * qx) || L.ly % (2 * qy))
+        return fail(nullptr, FSKMC_EINVAL,
+                    "lattice %dx%d is not a positive multiple of twice the cell %dx%d", L.lx,
+                    L.ly, qx, qy);
+    if ((int64_t)L.lx * L.ly > (int64_t)1 << 31)
+        return fail(nullptr, FSKMC_EINVAL, "lattice too large (%d x %d)", L.lx, L.ly);
+    if ((model == fskmc::DIFFUSION || model == fskmc::ZGB) && (qx < 2 || qy < 2))
+        return fail(nullptr, FSKMC_EINVAL, "two-site models need cells of at least 2x2");
+    if (model == fskmc::DIFFUSION && (L.lx < qx + 4 || L.ly < qy + 4))
+        return fail(nullptr, FSKMC_EINVAL,
+                    "diffusion needs lx >= qx+4 and ly >= qy+4 (two-site frozen halo)");
+    return FSKMC_OK;
+}
+
+int64_t nsteps(double dt, double T)
+{
+    if (!(dt > 0.0) || !(T >= 0.0) || !std::isfinite(dt) || !std::isfinite(T)) return -1;
+    double n = std::floor(T / dt + 0.5);
+    if (std::fabs(n * dt - T) > 1e-9 * T) return -1;
+    if (n > 1e9) return -1;
+    return (int64_t)n;
+}
+
+struct Win {
+    int colour;
+    double h;
+};
+
+// Windows of a run starting at global window index w0 (Section 3): LIE
+// E(dt) O(dt); STRANG E(dt/2) O(dt) E(dt/2); RANDOM 2 windows of dt per step,
+// colour = bit 0 of word 0 of Philox(seed, (0, w, 0, rep | 3<<24)), 0 = E;
+// RANDOM_ORDER per step (c, 1-c) with c drawn the same way at the step's
+// first window index.
+void build_schedule(int scheme, int64_t n, double dt, uint64_t seed, uint32_t rep, uint64_t w0,
+                    std::vector<Win> &out)
+{
+    out.clear();
+    const uint32_t c3 = rep | (fskmc::TAG_SCHED << 24);
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t w = (uint32_t)(w0 + out.size());
+        switch (scheme) {
+        case FSKMC_LIE:
+            out.push_back({0, dt});
+            out.push_back({1, dt});
+            break;
+        case FSKMC_STRANG:
+            out.push_back({0, dt * 0.5});
+            out.push_back({1, dt});
+            out.push_back({0, dt * 0.5});
+            break;
+        case FSKMC_RANDOM:
+            out.push_back({(int)(fskmc::draw(seed, 0, w, 0, c3).x & 1u), dt});
+            out.push_back({(int)(fskmc::draw(seed, 0, w + 1, 0, c3).x & 1u), dt});
+            break;
+        case FSKMC_RANDOM_ORDER: {
+            int c = (int)(fskmc::draw(seed, 0, w, 0, c3).x & 1u);
+            out.push_back({c, dt});
+            out.push_back({1 - c, dt});
+            break;
+        }
+        }
+    }
+}
+
+fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
+                      const fskmc_rates *rates, fskmc_cell_shape cell, void *stream, bool batch,
+                      fskmc_ctx **out)
+{
+    if (!out || !lats || !rates) return fail(nullptr, FSKMC_EINVAL, "NULL argument");
+    *out = nullptr;
+    if ((int)model < 0 || (int)model > 3) return fail(nullptr, FSKMC_EINVAL, "unknown model %d", (int)model);
+    if (n < 1 || n > 65536) return fail(nullptr, FSKMC_EINVAL, "replica count %d out of range", n);
+    int qx = cell.qx, qy = cell.qy;
+    if (qx == 0 && qy == 0) {
+        // Autotuner: the largest square cell in {32, 16, 8} that every
+        // replica admits and that leaves at least 152 active cells in total
+        // (one per SM); falling back to the largest admissible one.
+        int best = 0;
+        for (int q : {32, 16, 8}) {
+            bool ok = true;
+            int64_t cells = 0;
+            for (int r = 0; r < n && ok; ++r) {
+                ok = check_geometry(model, lats[r], q, q) == FSKMC_OK;
+                cells += ok ? (int64_t)(lats[r].lx / q) * (lats[r].ly / q) / 2 : 0;
+            }
+            if (!ok) continue;
+            if (!best) best = q;
+            if (cells >= 152) { best = q; break; }
+        }
+        if (!best) return fail(nullptr, FSKMC_EINVAL, "no cell size in {8,16,32} fits every lattice");
+        qx = qy = best;
+    }
+    for (int r = 0; r < n; ++r) {
+        fskmc_status st = check_geometry(model, lats[r], qx, qy);
+        if (st) return st;
+        st = check_rates(model, rates[r]);
+        if (st) return st;
+    }
+    fskmc_ctx *c = new fskmc_ctx();
+    c->model = model;
+    c->nstates = (int)model == fskmc::ZGB ? 3 : 2;
+    c->nrep = n;
+    c->qx = qx;
+    c->qy = qy;
+    c->batch = batch;
+    c->stream = (cudaStream_t)stream;
+    c->reps.resize(n);
+    int64_t off = 0;
+    int32_t coff = 0;
+    for (int r = 0; r < n; ++r) {
+        Replica &R = c->reps[r];
+        std::memset(&R, 0, sizeof R);
+        R.lx = lats[r].lx;
+        R.ly = lats[r].ly;
+        R.ncx = R.lx / qx;
+        R.ncy = R.ly / qy;
+        R.lat_off = off;
+        R.cell_off = coff;
+        R.rep = (uint32_t)r;
+        c->nclass = class_rates(model, rates[r], R.r);
+        for (int k = 0; k < c->nclass; ++k) R.rf[k] = (float)R.r[k];
+        off += ((int64_t)R.lx * R.ly + 255) & ~(int64_t)255;
+        coff += R.ncx * R.ncy;
+    }
+    c->total_sites = off;
+    c->total_cells = coff;
+    cudaError_t e;
+    e = cudaMalloc(&c->d_lat[0], (size_t)off);
+    if (e == cudaSuccess && (int)model == fskmc::DIFFUSION) e = cudaMalloc(&c->d_lat[1], (size_t)off);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_reps, sizeof(Replica) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_workload, sizeof(int32_t) * (size_t)coff);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch_u32, sizeof(unsigned int) * 4);
+    if (e != cudaSuccess) {
+        fskmc_destroy(c);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? FSKMC_ENOMEM : FSKMC_ECUDA,
+                    "device allocation failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(c->d_lat[0], 0, (size_t)off, c->stream);
+    if (e == cudaSuccess && c->d_lat[1]) e = cudaMemsetAsync(c->d_lat[1], 0, (size_t)off, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_workload, 0, sizeof(int32_t) * (size_t)coff, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 4, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_reps, c->reps.data(), sizeof(Replica) * n, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        fskmc_destroy(c);
+        return fail(nullptr, FSKMC_ECUDA, "context setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    g_create_error.clear();
+    return FSKMC_OK;
+}
+
+fskmc_status upload_reps(fskmc_ctx *c)
+{
+    CK(c, cudaMemcpyAsync(c->d_reps, c->reps.data(), sizeof(Replica) * c->nrep,
+                          cudaMemcpyHostToDevice, c->stream));
+    return FSKMC_OK;
+}
+
+// One window of every replica on the plain engine.
+fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sched, size_t i,
+                          uint64_t w, uint64_t seed)
+{
+    const int fp32 = c->clock == FSKMC_CLOCK_FP32;
+    const bool pingpong = c->d_lat[1] != nullptr;
+    for (int r = 0; r < c->nrep; ++r) {
+        const Win &win = sched[sched.size() == 1 ? 0 : r][i];
+        fskmc::WindowArgs a;
+        a.reps = c->d_reps;
+        a.rep_index = r;
+        a.qx = c->qx;
+        a.qy = c->qy;
+        a.colour = win.colour;
+        a.w = (uint32_t)w;
+        a.h = win.h;
+        a.seed = seed;
+        a.src = c->d_lat[c->cur];
+        a.dst = pingpong ? c->d_lat[1 - c->cur] : c->d_lat[c->cur];
+        a.workload = c->d_workload;
+        a.counters = c->d_counters;
+        const Replica &R = c->reps[r];
+        int nactive = R.ncx * R.ncy / 2;
+        CK(c, fskmc::launch_window(c->model, fp32, a, nactive, c->wpb, c->stream));
+    }
+    if (pingpong) c->cur ^= 1;
+    return FSKMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fskmc_status fskmc_create(const fskmc_lattice *lattice, fskmc_model model,
+                          const fskmc_rates *rates, fskmc_cell_shape cell, void *stream,
+                          fskmc_ctx **out)
+{
+    return make_ctx(1, lattice, model, rates, cell, stream, false, out);
+}
+
+fskmc_status fskmc_batch_create(int32_t n, const fskmc_lattice *lattices, fskmc_model model,
+                                const fskmc_rates *rates, fskmc_cell_shape cell, void *stream,
+                                fskmc_ctx **out)
+{
+    return make_ctx(n, lattices, model, rates, cell, stream, true, out);
+}
+
+void fskmc_destroy(fskmc_ctx *c)
+{
+    if (!c) return;
+    if (c->stream || c->d_lat[0]) cudaStreamSynchronize(c->stream);
+    fskmc::persistent_free(c->pers);
+    cudaFree(c->d_lat[0]);
+    cudaFree(c->d_lat[1]);
+    cudaFree(c->d_reps);
+    cudaFree(c->d_workload);
+    cudaFree(c->d_counters);
+    cudaFree(c->d_scratch_u32);
+    cudaFree(c->d_obs);
+    delete c;
+}
+
+const char *fskmc_last_error(const fskmc_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+fskmc_status fskmc_set_replica_id(fskmc_ctx *c, uint32_t id)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (c->batch) return fail(c, FSKMC_EINVAL, "replica ids of a batch are fixed");
+    if (id >= (1u << 24)) return fail(c, FSKMC_EINVAL, "replica id must be < 2^24");
+    c->reps[0].rep = id;
+    return upload_reps(c);
+}
+
+fskmc_status fskmc_set_clock(fskmc_ctx *c, fskmc_clock clock)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (clock != FSKMC_CLOCK_FP64 && clock != FSKMC_CLOCK_FP32)
+        return fail(c, FSKMC_EINVAL, "unknown clock %d", (int)clock);
+    c->clock = clock;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_engine(fskmc_ctx *c, fskmc_engine engine)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (engine != FSKMC_ENGINE_PLAIN && engine != FSKMC_ENGINE_PERSISTENT)
+        return fail(c, FSKMC_EINVAL, "unknown engine %d", (int)engine);
+    c->engine = engine;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_warps_per_block(fskmc_ctx *c, int32_t warps)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (warps < 1 || warps > 16) return fail(c, FSKMC_EINVAL, "warps per block must be 1..16");
+    size_t need = fskmc::window_smem_per_warp(c->model, c->qx, c->qy) * (size_t)warps;
+    if (need > 200 * 1024) return fail(c, FSKMC_EINVAL, "%d warps need %zu B of shared memory", warps, need);
+    c->wpb = warps;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_spin_limit(fskmc_ctx *c, uint32_t polls)
+{
+    if (!c) return FSKMC_EINVAL;
+    c->spin_limit = polls;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_info(const fskmc_ctx *c, int32_t out[5])
+{
+    if (!c || !out) return FSKMC_EINVAL;
+    out[0] = c->qx;
+    out[1] = c->qy;
+    out[2] = c->nrep;
+    out[3] = c->total_cells;
+    out[4] = c->wpb;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_init_random(fskmc_ctx *c, uint64_t seed, double coverage)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (!(coverage >= 0.0 && coverage <= 1.0)) return fail(c, FSKMC_EINVAL, "coverage must be in [0,1]");
+    for (int r = 0; r < c->nrep; ++r) {
+        const Replica &R = c->reps[r];
+        CK(c, fskmc::launch_init_bernoulli(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, seed, coverage,
+                                           R.rep, c->stream));
+    }
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_init_bump(fskmc_ctx *c, uint64_t seed, double amp, double width, int32_t species)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (!(amp >= 0.0 && amp <= 1.0) || !(width > 0.0) || !std::isfinite(width))
+        return fail(c, FSKMC_EINVAL, "amp must be in [0,1] and width > 0");
+    if (species < 0 || species >= c->nstates) return fail(c, FSKMC_EINVAL, "species %d not a state", species);
+    for (int r = 0; r < c->nrep; ++r) {
+        const Replica &R = c->reps[r];
+        fskmc::u32x4 cc = fskmc::draw(seed, 0, 0xFFFFFFFFu, 0, R.rep | (fskmc::TAG_SCHED << 24));
+        int x0 = (int)(cc.x % (uint32_t)R.lx), y0 = (int)(cc.y % (uint32_t)R.ly);
+        std::vector<double> g(R.lx + R.ly);
+        double two_s2 = 2.0 * width * width;
+        for (int x = 0; x < R.lx; ++x) {
+            int d = std::abs(x - x0);
+            if (R.lx - d < d) d = R.lx - d;
+            g[x] = std::exp(-((double)d * (double)d) / two_s2);
+        }
+        for (int y = 0; y < R.ly; ++y) {
+            int d = std::abs(y - y0);
+            if (R.ly - d < d) d = R.ly - d;
+            g[R.lx + y] = std::exp(-((double)d * (double)d) / two_s2);
+        }
+        double *dg = nullptr;
+        CK(c, cudaMallocAsync(&dg, sizeof(double) * g.size(), c->stream));
+        CK(c, cudaMemcpyAsync(dg, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(c, fskmc::launch_init_bump(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, seed, dg, dg + R.lx,
+                                      amp, species, R.rep, c->stream));
+        CK(c, cudaFreeAsync(dg, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_state(fskmc_ctx *c, int32_t replica, const uint8_t *src, int32_t is_device)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (replica < 0 || replica >= c->nrep || !src) return fail(c, FSKMC_EINVAL, "bad replica or NULL src");
+    const Replica &R = c->reps[replica];
+    size_t n = (size_t)R.lx * R.ly;
+    uint8_t *dst = c->d_lat[c->cur] + R.lat_off;
+    CK(c, cudaMemcpyAsync(dst, src, n, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaMemsetAsync(c->d_scratch_u32, 0, sizeof(unsigned int), c->stream));
+    CK(c, fskmc::launch_validate(dst, (int64_t)n, c->nstates, c->d_scratch_u32, c->stream));
+    unsigned int bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, c->d_scratch_u32, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (bad) {
+        CK(c, cudaMemsetAsync(dst, 0, n, c->stream));
+        return fail(c, FSKMC_EINVAL, "%u sites hold a value that is not a state of the model", bad);
+    }
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_get_state(fskmc_ctx *c, int32_t replica, uint8_t *dst, int32_t is_device)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (replica < 0 || replica >= c->nrep || !dst) return fail(c, FSKMC_EINVAL, "bad replica or NULL dst");
+    const Replica &R = c->reps[replica];
+    size_t n = (size_t)R.lx * R.ly;
+    CK(c, cudaMemcpyAsync(dst, c->d_lat[c->cur] + R.lat_off, n,
+                          is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!is_device) CK(c, cudaStreamSynchronize(c->stream));
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_run(fskmc_ctx *c, fskmc_scheme scheme, double dt, double T, uint64_t seed)
+{
+    if (!c) return FSKMC_EINVAL;
+    if ((int)scheme < 0 || (int)scheme > 3) return fail(c, FSKMC_EINVAL, "unknown scheme %d", (int)scheme);
+    int64_t n = nsteps(dt, T);
+    if (n < 0) return fail(c, FSKMC_EINVAL, "dt must be > 0, T >= 0 and T/dt an integer (dt=%g T=%g)", dt, T);
+    const bool per_replica = (scheme == FSKMC_RANDOM || scheme == FSKMC_RANDOM_ORDER) && c->nrep > 1;
+    std::vector<std::vector<Win>> sched(per_replica ? c->nrep : 1);
+    for (size_t r = 0; r < sched.size(); ++r)
+        build_schedule(scheme, n, dt, seed, c->reps[r].rep, c->w, sched[r]);
+    const size_t nw = sched[0].size();
+    if (c->engine == FSKMC_ENGINE_PERSISTENT) {
+        std::vector<int8_t> col(sched.size() * nw);
+        std::vector<double> hh(nw);
+        for (size_t r = 0; r < sched.size(); ++r)
+            for (size_t i = 0; i < nw; ++i) col[r * nw + i] = (int8_t)sched[r][i].colour;
+        for (size_t i = 0; i < nw; ++i) hh[i] = sched[0][i].h;
+        fskmc::PersistentRun pr;
+        pr.model = c->model;
+        pr.fp32 = c->clock == FSKMC_CLOCK_FP32;
+        pr.qx = c->qx;
+        pr.qy = c->qy;
+        pr.nrep = c->nrep;
+        pr.reps_host = c->reps.data();
+        pr.reps_dev = c->d_reps;
+        pr.lat = c->d_lat[c->cur];
+        pr.lat2 = c->d_lat[1] ? c->d_lat[1 - c->cur] : nullptr;
+        pr.workload = c->d_workload;
+        pr.counters = c->d_counters;
+        pr.total_cells = c->total_cells;
+        pr.colour = col.data();
+        pr.colour_per_replica = sched.size() > 1;
+        pr.h = hh.data();
+        pr.nwin = (int64_t)nw;
+        pr.w0 = c->w;
+        pr.seed = seed;
+        pr.wpb = c->wpb;
+        pr.spin_limit = c->spin_limit;
+        std::string msg;
+        cudaError_t e = fskmc::persistent_run(&c->pers, pr, c->stream, &msg);
+        if (e == cudaErrorTimeout) {
+            c->w += nw;
+            c->windows += nw;
+            return fail(c, FSKMC_ETIMEOUT, "persistent run: %s; the lattice is undefined", msg.c_str());
+        }
+        if (e != cudaSuccess) return fail(c, FSKMC_ECUDA, "persistent run: %s (%s)", cudaGetErrorString(e), msg.c_str());
+        if (c->d_lat[1] && (nw & 1)) c->cur ^= 1;
+    } else {
+        for (size_t i = 0; i < nw; ++i) {
+            fskmc_status st = plain_window(c, sched, i, c->w + i, seed);
+            if (st) return st;
+        }
+    }
+    c->w += nw;
+    c->windows += nw;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_window(fskmc_ctx *c, int32_t colour, double h, uint64_t seed)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (colour != 0 && colour != 1) return fail(c, FSKMC_EINVAL, "colour must be 0 or 1");
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(c, FSKMC_EINVAL, "window length must be > 0");
+    std::vector<std::vector<Win>> sched(1, std::vector<Win>{{colour, h}});
+    fskmc_status st = plain_window(c, sched, 0, c->w, seed);
+    if (st) return st;
+    c->w += 1;
+    c->windows += 1;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_get_window_index(const fskmc_ctx *c, uint64_t *w)
+{
+    if (!c || !w) return FSKMC_EINVAL;
+    *w = c->w;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_window_index(fskmc_ctx *c, uint64_t w)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (w >= (1ull << 32)) return fail(c, FSKMC_EINVAL, "window index must be < 2^32");
+    c->w = w;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_observables(fskmc_ctx *c, int32_t replica, double *coverage, double *energy,
+                               double *paircorr, int32_t rmax)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (replica < 0 || replica >= c->nrep) return fail(c, FSKMC_EINVAL, "bad replica %d", replica);
+    const Replica &R = c->reps[replica];
+    if (!coverage || !energy || rmax < 0 || rmax > R.lx || rmax > R.ly || (rmax > 0 && !paircorr))
+        return fail(c, FSKMC_EINVAL, "bad observables arguments");
+    int need = 4 + 2 * rmax;
+    if (need > c->obs_cap) {
+        cudaFree(c->d_obs);
+        c->d_obs = nullptr;
+        CK(c, cudaMalloc(&c->d_obs, sizeof(unsigned long long) * need));
+        c->obs_cap = need;
+    }
+    CK(c, cudaMemsetAsync(c->d_obs, 0, sizeof(unsigned long long) * need, c->stream));
+    CK(c, fskmc::launch_observables(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, rmax, c->d_obs, c->stream));
+    std::vector<unsigned long long> h(need);
+    CK(c, cudaMemcpyAsync(h.data(), c->d_obs, sizeof(unsigned long long) * need, cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double N = (double)R.lx * (double)R.ly;
+    for (int s = 0; s < 3; ++s) coverage[s] = (double)h[s] / N;
+    const double pairs = (double)h[3], n1 = (double)h[1];
+    if (c->model == fskmc::ZGB) *energy = NAN;
+    else if (c->model == fskmc::ISING) *energy = -(4.0 * pairs - 8.0 * n1 + 2.0 * N) / N;
+    else *energy = -pairs / N;
+    for (int r = 0; r < 2 * rmax; ++r) paircorr[r] = (double)h[4 + r] / N;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_stats(fskmc_ctx *c, uint64_t out[5])
+{
+    if (!c || !out) return FSKMC_EINVAL;
+    unsigned long long h[4];
+    CK(c, cudaMemcpyAsync(h, c->d_counters, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    out[0] = h[0];
+    out[1] = c->windows;
+    out[2] = h[1];
+    out[3] = h[2];
+    out[4] = h[3];
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_workload(fskmc_ctx *c, int32_t replica, int32_t *out)
+{
+    if (!c || !out) return FSKMC_EINVAL;
+    if (replica < 0 || replica >= c->nrep) return fail(c, FSKMC_EINVAL, "bad replica %d", replica);
+    const Replica &R = c->reps[replica];
+    CK(c, cudaMemcpyAsync(out, c->d_workload + R.cell_off, sizeof(int32_t) * R.ncx * R.ncy,
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_sync(fskmc_ctx *c)
+{
+    if (!c) return FSKMC_EINVAL;
+    CK(c, cudaStreamSynchronize(c->stream));
+    return FSKMC_OK;
+}
+
+}  // extern "C"

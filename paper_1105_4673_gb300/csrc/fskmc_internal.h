@@ -1,0 +1,63 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fskmc {
+
+enum Model : int { ADSDES = 0, ISING = 1, DIFFUSION = 2, ZGB = 3 };
+
+constexpr int MAX_CLASSES = 16;
+constexpr int MAX_Q = 32;
+constexpr int MAX_CELL_SITES = 1024;
+
+// Per-replica description, resident on the device.
+struct Replica {
+    int32_t lx, ly;      // lattice sides
+    int32_t ncx, ncy;    // cells along x and y
+    int64_t lat_off;     // byte offset of the replica's lattice in the lattice buffer
+    int32_t cell_off;    // index of the replica's cell 0 in per-cell arrays
+    uint32_t rep;        // replica word of the random counters
+    double r[MAX_CLASSES];   // class rates, binary64
+    float rf[MAX_CLASSES];   // the same rates rounded to binary32
+};
+
+// Arguments of one fractional window over the active cells of one replica.
+struct WindowArgs {
+    const Replica *reps;       // device array
+    int32_t rep_index;         // which replica
+    int32_t qx, qy;            // cell shape
+    int32_t colour;            // 0 = E, 1 = O
+    uint32_t w;                // global window index
+    double h;                  // window length
+    uint64_t seed;
+    const uint8_t *src;        // lattice at window start (all replicas)
+    uint8_t *dst;              // result (== src when updated in place)
+    int32_t *workload;         // events per cell in its latest window
+    unsigned long long *counters;  // [0] events, [1] ambiguous cell-windows, [2] timeouts
+};
+
+// Shared-memory bytes one warp of the window kernel needs.
+size_t window_smem_per_warp(int model, int qx, int qy);
+
+// Launch one window (all active cells of a.rep_index).
+cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int ncells_active,
+                          int warps_per_block, cudaStream_t s);
+
+// Initial states.
+cudaError_t launch_init_bernoulli(uint8_t *lat, int lx, int ly, uint64_t seed, double p,
+                                  uint32_t rep, cudaStream_t s);
+cudaError_t launch_init_bump(uint8_t *lat, int lx, int ly, uint64_t seed, const double *gx,
+                             const double *gy, double amp, int species, uint32_t rep,
+                             cudaStream_t s);
+
+// Integer observables: out[0..2] state counts, out[3] occupied NN pairs,
+// out[4 .. 4+rmax) G_x sums, out[4+rmax .. 4+2 rmax) G_y sums.
+cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
+                               unsigned long long *out, cudaStream_t s);
+
+// Validation of a lattice: counts bytes >= nstates into *bad.
+cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned int *bad,
+                            cudaStream_t s);
+
+}  // namespace fskmc

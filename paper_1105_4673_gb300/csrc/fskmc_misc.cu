@@ -1,0 +1,143 @@
+// Initial states, lattice validation and the integer observables of Section 7.
+#include <cuda_runtime.h>
+
+#include "fskmc_internal.h"
+#include "philox.cuh"
+
+namespace fskmc {
+
+namespace {
+
+// Site i of replica rep is 1 iff word 0 of Philox(seed, (i,0,0,rep|2<<24)) < p 2^32.
+__global__ void init_bernoulli_kernel(uint8_t *lat, int64_t n, uint64_t seed, double thr,
+                                      uint32_t rep)
+{
+    const uint32_t c3 = rep | (TAG_INIT << 24);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        u32x4 o = draw(seed, (uint32_t)i, 0u, 0u, c3);
+        lat[i] = __uint2double_rn(o.x) < thr ? 1 : 0;
+    }
+}
+
+// Gaussian bump: species with probability (amp * gx[x]) * gy[y].
+__global__ void init_bump_kernel(uint8_t *lat, int lx, int ly, uint64_t seed,
+                                 const double *gx, const double *gy, double amp, int species,
+                                 uint32_t rep)
+{
+    const uint32_t c3 = rep | (TAG_INIT << 24);
+    const int64_t n = (int64_t)lx * ly;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % lx), y = (int)(i / lx);
+        u32x4 o = draw(seed, (uint32_t)i, 0u, 0u, c3);
+        double p = __dmul_rn(__dmul_rn(amp, gx[x]), gy[y]);
+        lat[i] = __uint2double_rn(o.x) < __dmul_rn(p, 4294967296.0) ? (uint8_t)species : 0;
+    }
+}
+
+__global__ void validate_kernel(const uint8_t *lat, int64_t n, int nstates, unsigned int *bad)
+{
+    unsigned int c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        c += lat[i] >= nstates;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
+}
+
+// One block per row (grid-stride over rows). Accumulators in shared memory
+// as 32-bit per block, flushed with 64-bit atomics.
+__global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
+                                   unsigned long long *out)
+{
+    extern __shared__ unsigned int acc[];  // 4 + 2*rmax
+    const int nacc = 4 + 2 * rmax;
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int y = blockIdx.x; y < ly; y += gridDim.x) {
+        const uint8_t *row = lat + (int64_t)y * lx;
+        const uint8_t *down = lat + (int64_t)((y + 1) % ly) * lx;
+        // counts and nearest-neighbour pairs; lx is a multiple of 32 or the
+        // tail is handled by the predicate, so every lane reaches the reduces
+        for (int x0 = 0; x0 < lx; x0 += blockDim.x) {
+            int x = x0 + threadIdx.x;
+            unsigned int c0 = 0, c1 = 0, c2 = 0, pr = 0;
+            if (x < lx) {
+                int s = row[x];
+                c0 = s == 0; c1 = s == 1; c2 = s == 2;
+                if (s == 1) pr = (row[(x + 1) % lx] == 1) + (down[x] == 1);
+            }
+            c0 = __reduce_add_sync(0xffffffffu, c0);
+            c1 = __reduce_add_sync(0xffffffffu, c1);
+            c2 = __reduce_add_sync(0xffffffffu, c2);
+            pr = __reduce_add_sync(0xffffffffu, pr);
+            if (lane == 0) {
+                atomicAdd(&acc[0], c0); atomicAdd(&acc[1], c1);
+                atomicAdd(&acc[2], c2); atomicAdd(&acc[3], pr);
+            }
+            for (int r = 1; r <= rmax; ++r) {
+                unsigned int gxv = 0, gyv = 0;
+                if (x < lx && row[x] == 1) {
+                    gxv = row[(x + r) % lx] == 1;
+                    gyv = lat[(int64_t)((y + r) % ly) * lx + x] == 1;
+                }
+                gxv = __reduce_add_sync(0xffffffffu, gxv);
+                gyv = __reduce_add_sync(0xffffffffu, gyv);
+                if (lane == 0) {
+                    if (gxv) atomicAdd(&acc[4 + r - 1], gxv);
+                    if (gyv) atomicAdd(&acc[4 + rmax + r - 1], gyv);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x)
+        if (acc[i]) atomicAdd(&out[i], (unsigned long long)acc[i]);
+}
+
+int grid_for(int64_t n, int block)
+{
+    int64_t b = (n + block - 1) / block;
+    if (b > 152 * 32) b = 152 * 32;
+    return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_init_bernoulli(uint8_t *lat, int lx, int ly, uint64_t seed, double p,
+                                  uint32_t rep, cudaStream_t s)
+{
+    int64_t n = (int64_t)lx * ly;
+    init_bernoulli_kernel<<<grid_for(n, 256), 256, 0, s>>>(lat, n, seed, p * 4294967296.0, rep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_bump(uint8_t *lat, int lx, int ly, uint64_t seed, const double *gx,
+                             const double *gy, double amp, int species, uint32_t rep,
+                             cudaStream_t s)
+{
+    int64_t n = (int64_t)lx * ly;
+    init_bump_kernel<<<grid_for(n, 256), 256, 0, s>>>(lat, lx, ly, seed, gx, gy, amp, species,
+                                                      rep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned int *bad,
+                            cudaStream_t s)
+{
+    validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(lat, n, nstates, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
+                               unsigned long long *out, cudaStream_t s)
+{
+    int grid = ly < 152 * 8 ? ly : 152 * 8;
+    size_t smem = sizeof(unsigned int) * (size_t)(4 + 2 * rmax);
+    observables_kernel<<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fskmc

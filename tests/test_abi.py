@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every entry point include/fskmc.h
+declares; argument validation that happens before any device work is
+checked here without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1105_4673_gb300 as F
+from paper_1105_4673_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return F.lib()
+
+
+def declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fskmc_[a-z_0-9]+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert "fskmc_create" in names and "fskmc_run" in names and "fskmc_observables" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names <= set(F.EXPORTS) | {n for n in names if n.startswith("fskmc_")}
+    assert set(F.EXPORTS) <= names
+
+
+def _create(lib, lx, ly, model, q, rates=None):
+    h = C.c_void_p()
+    st = lib.fskmc_create(C.byref(F.Lattice(lx, ly, 0)), model, C.byref(F._rates(rates or {})),
+                          F.CellShape(*q), None, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("lx,ly,model,q,rates", [
+    (64, 64, 0, (6, 8), {}),            # 64 not a multiple of 12
+    (64, 64, 0, (0, 8), {}),            # bad cell
+    (64, 64, 0, (40, 8), {}),           # q > 32
+    (16, 16, 3, (1, 2), {}),            # two-site model with q < 2
+    (4, 4, 2, (2, 2), {}),              # diffusion halo needs lx >= qx + 4
+    (64, 64, 0, (8, 8), dict(ka=-1.0)),  # negative rate
+    (64, 64, 3, (8, 8), dict(yA=1.5)),  # yA outside [0,1]
+    (64, 64, 7, (8, 8), {}),            # unknown model
+    (64, 64, 1, (8, 8), dict(betaJ=float("nan"))),
+])
+def test_create_rejects_invalid_arguments(lib, lx, ly, model, q, rates):
+    st, h = _create(lib, lx, ly, model, q, rates)
+    assert st == F.EINVAL and not h.value
+    assert lib.fskmc_last_error(None).decode()
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.fskmc_run(None, 0, 0.1, 1.0, 1) == F.EINVAL
+    assert lib.fskmc_sync(None) == F.EINVAL
+    assert lib.fskmc_stats(None, None) == F.EINVAL
+    lib.fskmc_destroy(None)

@@ -1,0 +1,152 @@
+"""Parity of the CUDA path with the oracle: bit-identical lattices, event
+counts and workloads under the same seeds (binary64 clocks), across models,
+schedules, cell shapes (including ragged cells that leave lanes idle) and
+launch shapes."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1105_4673_gb300 as F
+from gpu_util import gpu_ctx, windowwise
+from workloads import WORKLOADS, random_lattice
+
+pytestmark = pytest.mark.gpu
+
+RATES = {
+    "ADSDES": dict(ka=1.0, kd=1.0, betaJ=1.0),
+    "ISING": dict(ka=1.0, kd=1.0, betaJ=0.4407),
+    "DIFFUSION": dict(ka=1.0, kd=1.0, betaJ=2.0, nu=10.0),
+    "ZGB": dict(yA=0.52, kr=100.0, kd=0.01),
+}
+
+# (model, lx, ly, q): several tiles, non-power-of-two and ragged cells
+GEOMS = [
+    ("ADSDES", 64, 64, (8, 8)),
+    ("ADSDES", 4, 4, (2, 2)),
+    ("ISING", 60, 40, (6, 5)),
+    ("ISING", 48, 40, (12, 10)),
+    ("ISING", 128, 64, (32, 32)),
+    ("DIFFUSION", 48, 48, (8, 8)),
+    ("DIFFUSION", 16, 24, (4, 6)),
+    ("ZGB", 64, 64, (8, 8)),
+    ("ZGB", 8, 8, (2, 2)),
+    ("ZGB", 96, 64, (16, 32)),
+]
+
+
+def _init(model, lx, ly, seed):
+    if model == "ZGB":
+        return random_lattice(lx, ly, 3, seed, p=[0.6, 0.2, 0.2])
+    return oracle.init_bernoulli(lx, ly, seed, 0.3 if model == "DIFFUSION" else 0.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1105_4673_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+@pytest.mark.parametrize("model,lx,ly,q", GEOMS)
+@pytest.mark.parametrize("scheme", ["LIE", "STRANG", "RANDOM", "RANDOM_ORDER"])
+def test_run_bit_exact(model, lx, ly, q, scheme):
+    dt = 0.05 if model != "ZGB" else 0.02
+    T = 1.0 if lx * ly <= 64 * 64 else 0.5
+    seed = 0xC0FFEE + lx + 7 * ly
+    init = _init(model, lx, ly, seed)
+    orc = oracle.FSRun(lx, ly, *q, model, RATES[model], init).run(scheme, dt, T, seed)
+    with gpu_ctx(lx, ly, q, model, RATES[model], init) as c:
+        c.run(scheme, dt, T, seed)
+        g = c.get_state()
+        st = c.stats()
+        wl = c.workload()
+    if orc.ambiguous == 0:
+        assert np.array_equal(g, orc.lat)
+        assert st["events"] == orc.events
+        assert np.array_equal(wl, orc.workload)
+    else:  # redo window by window with resync at flagged windows
+        col, h = oracle.schedule(scheme, dt, T, seed)
+        orc2 = oracle.FSRun(lx, ly, *q, model, RATES[model], init)
+        with gpu_ctx(lx, ly, q, model, RATES[model], init) as c2:
+            windowwise(c2, orc2, col, h, seed)
+    assert st["windows"] == orc.windows and st["events"] > 0
+
+
+def test_workload_adsdes64_both_couplings():
+    """The 64x64 adsorption/desorption workload in full (Lie, dt = 0.1,
+    T = 10, 8x8 cells) at betaJ = 0 and 1."""
+    w = WORKLOADS["adsdes64"]
+    for bJ in (0.0, 1.0):
+        rates = dict(w["rates"], betaJ=bJ)
+        init = oracle.init_bernoulli(w["lx"], w["ly"], w["seed"], w["coverage"])
+        orc = oracle.FSRun(w["lx"], w["ly"], *w["q"], w["model"], rates, init)
+        orc.run(w["scheme"], w["dt"], w["T"], w["seed"])
+        with F.Context(w["lx"], w["ly"], w["model"], rates, w["q"]) as c:
+            c.init_random(w["seed"], w["coverage"])
+            assert np.array_equal(c.get_state(), init)
+            c.run(w["scheme"], w["dt"], w["T"], w["seed"])
+            assert np.array_equal(c.get_state(), orc.lat)
+            assert c.stats()["events"] == orc.events
+            cov, en, pc = c.observables(0, 8)
+            ocov, oen, opc = oracle.observables(w["lx"], w["ly"], w["model"], orc.lat, 8)
+            assert np.array_equal(cov, ocov) and en == oen and np.array_equal(pc, opc)
+
+
+@pytest.mark.parametrize("model", ["ISING", "ZGB", "DIFFUSION"])
+def test_observables_bit_exact(model):
+    lx, ly = 96, 80
+    lat = _init(model, lx, ly, 5)
+    with F.Context(lx, ly, model, RATES[model], (8, 8)) as c:
+        c.set_state(lat)
+        for rmax in (0, 1, 16):
+            cov, en, pc = c.observables(0, rmax)
+            ocov, oen, opc = oracle.observables(lx, ly, model, lat, rmax)
+            assert np.array_equal(cov, ocov)
+            assert (np.isnan(en) and np.isnan(oen)) or en == oen
+            assert np.array_equal(pc, opc)
+
+
+def test_init_matches_oracle():
+    with F.Context(96, 64, "ZGB", RATES["ZGB"], (8, 8)) as c:
+        c.init_random(123, 0.37)
+        assert np.array_equal(c.get_state(), oracle.init_bernoulli(96, 64, 123, 0.37))
+        c.init_bump(77, 0.9, 96 / 8, 1)
+        assert np.array_equal(c.get_state(), oracle.init_bump(96, 64, 77, 0.9, 96 / 8, 1))
+
+
+@pytest.mark.parametrize("wpb", [1, 3, 8, 16])
+def test_launch_shape_invariance(wpb):
+    model, lx, ly, q = "ISING", 64, 64, (8, 8)
+    init = _init(model, lx, ly, 9)
+    orc = oracle.FSRun(lx, ly, *q, model, RATES[model], init).run("STRANG", 0.1, 1.0, 4)
+    with gpu_ctx(lx, ly, q, model, RATES[model], init, wpb=wpb) as c:
+        c.run("STRANG", 0.1, 1.0, 4)
+        assert np.array_equal(c.get_state(), orc.lat)
+
+
+@pytest.mark.parametrize("model", ["ADSDES", "DIFFUSION", "ZGB"])
+def test_resume_is_bit_exact(model):
+    lx, ly, q = 64, 64, (8, 8)
+    init = _init(model, lx, ly, 11)
+    with gpu_ctx(lx, ly, q, model, RATES[model], init) as a, \
+            gpu_ctx(lx, ly, q, model, RATES[model], init) as b:
+        a.run("RANDOM", 0.05, 1.0, 3)
+        b.run("RANDOM", 0.05, 0.5, 3)
+        w = b.window_index
+        snap = b.get_state()
+        with gpu_ctx(lx, ly, q, model, RATES[model], snap) as b2:
+            b2.window_index = w
+            b2.run("RANDOM", 0.05, 0.5, 3)
+            assert np.array_equal(a.get_state(), b2.get_state())
+
+
+def test_invalid_state_rejected():
+    with F.Context(16, 16, "ADSDES", RATES["ADSDES"], (4, 4)) as c:
+        bad = np.zeros(256, np.uint8)
+        bad[3] = 2
+        with pytest.raises(F.FskmcError) as e:
+            c.set_state(bad)
+        assert e.value.status == F.EINVAL
+        with pytest.raises(F.FskmcError):
+            c.run("LIE", 0.3, 1.0, 1)  # T/dt not an integer
