@@ -229,6 +229,37 @@ fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);
 /* Wait until all work queued on the context's stream has finished. */
 fskmc_status fskmc_sync(fskmc_ctx *ctx);
 
+/*
+ * Observables of a lattice already in device memory, computed without
+ * allocating any memory. The paper has no counterpart: this exists for
+ * callers that cannot let a library allocate -- applications whose device
+ * memory belongs to their own pool (a framework's caching allocator, a
+ * pre-reserved arena), and diagnostics that read the state after an
+ * out-of-memory error. No context is needed.
+ *
+ * lattice: device pointer to lx*ly bytes (row-major, states of `model`).
+ * stream: cudaStream_t to run on (NULL = legacy default stream); the call
+ * waits for it before returning. Outputs as in fskmc_observables (host
+ * memory): coverage[3], *energy, paircorr[2*rmax].
+ *
+ * The integer accumulators live in one fixed device array of
+ * 4 + 2*FSKMC_NOALLOC_MAX_RMAX 64-bit words that every GPU loading the
+ * library keeps until the process exits; each call clears the part it
+ * uses. All calls share that array, so calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong sums: serialise them.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. The call allocates neither device nor host heap memory.
+ *
+ * EINVAL: NULL lattice/coverage/energy (or paircorr with rmax > 0), unknown
+ * model, lx or ly < 1, lx*ly > 2^31, rmax < 0, rmax > min(lx, ly) or
+ * rmax > FSKMC_NOALLOC_MAX_RMAX. ECUDA: a CUDA call failed.
+ */
+#define FSKMC_NOALLOC_MAX_RMAX 256
+fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_t lx, int32_t ly,
+                                       fskmc_model model, void *stream, double *coverage,
+                                       double *energy, double *paircorr, int32_t rmax);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,7 +35,9 @@ EXPORTS = [
     "fskmc_set_spin_limit", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
+    "fskmc_observables_noalloc",
 ]
+NOALLOC_MAX_RMAX = 256
 
 
 class FskmcError(RuntimeError):
@@ -95,6 +97,9 @@ def lib():
             "fskmc_stats": ([vp, C.POINTER(C.c_uint64)], C.c_int),
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
+            "fskmc_observables_noalloc": ([vp, C.c_int32, C.c_int32, C.c_int, vp,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                           C.POINTER(C.c_double), C.c_int32], C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -261,3 +266,19 @@ class Context:
 
     def sync(self):
         _check(lib().fskmc_sync(self.h), self.h)
+
+
+def observables_noalloc(lattice, lx: int, ly: int, model, rmax: int = 0, stream=None):
+    """fskmc_observables_noalloc on a device lattice (a CUDA uint8 tensor or a
+    raw device pointer): the observables without any allocation by the
+    library. Calls that overlap on the GPU share one scratch array and race."""
+    p = lattice if isinstance(lattice, int) else lattice.data_ptr()
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    cov = (C.c_double * 3)()
+    en = C.c_double()
+    pc = (C.c_double * max(2 * rmax, 1))()
+    st = lib().fskmc_observables_noalloc(p, lx, ly, m, _stream_ptr(stream), cov, C.byref(en), pc,
+                                         rmax)
+    if st != OK:
+        raise FskmcError(st, "fskmc_observables_noalloc rejected the call")
+    return np.array(cov[:]), en.value, np.array(pc[:2 * rmax])

@@ -1,0 +1,85 @@
+// fskmc_observables_noalloc: the observables of a lattice that already sits
+// in device memory, computed without allocating anything.
+//
+// Some callers cannot let a library allocate device memory: applications
+// whose device memory is owned by their own pool (a framework's caching
+// allocator, a pre-reserved arena in a long-running service) must not have
+// cudaMalloc/cudaFree called behind their back, and a monitoring hook that
+// reads the state after an out-of-memory error has no memory left to get.
+// This entry point serves them: its integer accumulators live in a fixed,
+// file-scope device array that every GPU loading the library holds until
+// the process exits, and the call allocates neither device nor host heap
+// memory.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "fskmc.h"
+#include "fskmc_internal.h"
+
+namespace {
+
+// Room for the observables kernel's accumulators: 3 state counts, the pair
+// count and 2 * rmax correlation sums, rmax <= FSKMC_NOALLOC_MAX_RMAX.
+constexpr int kMaxSlots = 4 + 2 * FSKMC_NOALLOC_MAX_RMAX;
+static __device__ __align__(256) unsigned long long g_obs_scratch[kMaxSlots];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device. Looked up once
+// per device (with that device current) and cached; the host-side symbol
+// itself is not a device address and is never handed to a kernel.
+cudaError_t scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_obs_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_t lx, int32_t ly,
+                                                  fskmc_model model, void *stream,
+                                                  double *coverage, double *energy,
+                                                  double *paircorr, int32_t rmax)
+{
+    if (!lattice || !coverage || !energy) return FSKMC_EINVAL;
+    if ((int)model < 0 || (int)model > 3) return FSKMC_EINVAL;
+    if (lx < 1 || ly < 1 || (int64_t)lx * ly > ((int64_t)1 << 31)) return FSKMC_EINVAL;
+    if (rmax < 0 || rmax > FSKMC_NOALLOC_MAX_RMAX || rmax > lx || rmax > ly) return FSKMC_EINVAL;
+    if (rmax > 0 && !paircorr) return FSKMC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *scratch = nullptr;
+    if (scratch_address(&scratch) != cudaSuccess) return FSKMC_ECUDA;
+    unsigned long long *acc = static_cast<unsigned long long *>(scratch);
+    const int n = 4 + 2 * rmax;
+    // the array keeps the previous call's sums: clear the part this call uses
+    if (cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * n, s) != cudaSuccess) return FSKMC_ECUDA;
+    if (fskmc::launch_observables(lattice, lx, ly, rmax, acc, s) != cudaSuccess) return FSKMC_ECUDA;
+    unsigned long long h[kMaxSlots];
+    if (cudaMemcpyAsync(h, acc, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FSKMC_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FSKMC_ECUDA;
+    const double N = (double)lx * (double)ly;
+    for (int k = 0; k < 3; ++k) coverage[k] = (double)h[k] / N;
+    const double pairs = (double)h[3], n1 = (double)h[1];
+    if ((int)model == fskmc::ZGB) *energy = NAN;
+    else if ((int)model == fskmc::ISING) *energy = -(4.0 * pairs - 8.0 * n1 + 2.0 * N) / N;
+    else *energy = -pairs / N;
+    for (int r = 0; r < 2 * rmax; ++r) paircorr[r] = (double)h[4 + r] / N;
+    return FSKMC_OK;
+}
