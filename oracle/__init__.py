@@ -95,6 +95,10 @@ def lib():
         L.orc_ssa_ensemble.argtypes = [C.c_int, C.c_int, C.c_int, f64p, C.c_double, C.c_uint64,
                                        C.c_int, u8p, u8p]
         L.orc_ssa_ensemble.restype = C.c_int
+        L.orc_window_cells.argtypes = [C.c_int] * 5 + [f64p, C.c_int, C.c_double, C.c_uint32,
+                                                       C.c_uint64, C.c_uint32, u8p, C.c_int, i32p,
+                                                       i32p, i32p]
+        L.orc_window_cells.restype = C.c_int
         _lib = L
     return _lib
 
@@ -284,3 +288,17 @@ def ssa_ensemble(lx, ly, model, rates: dict, T, seed, M, init) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle rejected the ensemble arguments")
     return out
+
+
+def window_cells(lx, ly, qx, qy, model, rates: dict, lattice, colour: int, h: float, w: int,
+                 seed: int, cells, replica: int = 0):
+    """One window for the listed cells only; returns (lattice after, events, ambiguous)."""
+    lat = np.ascontiguousarray(lattice, dtype=np.uint8).reshape(-1).copy()
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    ev = np.zeros(len(cells), np.int32)
+    amb = np.zeros(len(cells), np.int32)
+    rc = lib().orc_window_cells(lx, ly, qx, qy, _model(model), _rates6(rates), colour, h, w, seed,
+                                replica, lat, len(cells), cells, ev, amb)
+    if rc != 0:
+        raise ValueError("oracle rejected the window arguments")
+    return lat, ev, amb

@@ -836,3 +836,34 @@ int orc_ssa_ensemble(int lx, int ly, int model, const double *rates6, double T,
     }
     return 0;
 }
+
+/* One window of colour col for the listed cells only (the sampled check of
+ * full-size lattices): every listed cell must have colour col; each runs
+ * against the lattice as it was when the window began and writes its write
+ * set into lat. events[i] receives cell cells[i]'s event count and amb[i]
+ * its ambiguity flag. Returns 0, or -1 on invalid arguments. */
+int orc_window_cells(int lx, int ly, int qx, int qy, int model,
+                     const double *rates6, int col, double h, uint32_t w,
+                     uint64_t seed, uint32_t rep, uint8_t *lat, int ncells,
+                     const int32_t *cells, int32_t *events, int32_t *amb)
+{
+    sys_t S;
+    if (qx < 1 || qy < 1 || lx % (2 * qx) || ly % (2 * qy)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates6)) return -1;
+    for (int i = 0; i < ncells; i++) {
+        int m = cells[i];
+        if (m < 0 || m >= S.ncx * S.ncy) return -1;
+        if ((((m % S.ncx) + (m / S.ncx)) & 1) != col) return -1;
+    }
+    work_t W;
+    if (work_init(&W, &S)) { work_free(&W); return -1; }
+    memcpy(W.snap, lat, (size_t)lx * ly);
+    for (int i = 0; i < ncells; i++) {
+        int m = cells[i], a = 0;
+        events[i] = (int32_t)cell_window(&W, lat, m % S.ncx, m / S.ncx, col, h, w, rep,
+                                         seed, &a);
+        amb[i] = a;
+    }
+    work_free(&W);
+    return 0;
+}

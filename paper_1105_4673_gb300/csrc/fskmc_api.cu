@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/fskmc.h: contexts, argument
 // validation, class-rate tables, processor communication schedules and the
 // plain (one launch per window) engine.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -199,6 +200,27 @@ void build_schedule(int scheme, int64_t n, double dt, uint64_t seed, uint32_t re
     }
 }
 
+// Fixed-point rates of the binary32-clock path: R_k = round(r_k 2^qshift)
+// with the largest qshift that keeps every cell's total rate below 2^62
+// (members per cell times the largest rate), so all rate-class sums are
+// exact 64-bit integers.
+void set_fixed_point(Replica &R, int nclass, int members)
+{
+    double rmax = 0.0;
+    for (int k = 0; k < nclass; ++k) rmax = std::max(rmax, R.r[k]);
+    int shift = 40;
+    if (rmax > 0.0) {
+        int ex = 0;
+        std::frexp((double)members * rmax, &ex);  // members * rmax < 2^ex
+        shift = 62 - ex;
+    }
+    shift = std::min(100, std::max(-100, shift));
+    R.qshift = shift;
+    R.qscale = std::ldexp(1.0f, -shift);
+    for (int k = 0; k < fskmc::MAX_CLASSES; ++k)
+        R.rq[k] = k < nclass ? (uint64_t)std::nearbyint(std::ldexp(R.r[k], shift)) : 0ull;
+}
+
 fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
                       const fskmc_rates *rates, fskmc_cell_shape cell, void *stream, bool batch,
                       fskmc_ctx **out)
@@ -255,7 +277,7 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
         R.cell_off = coff;
         R.rep = (uint32_t)r;
         c->nclass = class_rates(model, rates[r], R.r);
-        for (int k = 0; k < c->nclass; ++k) R.rf[k] = (float)R.r[k];
+        set_fixed_point(R, c->nclass, qx * qy * ((int)model >= fskmc::DIFFUSION ? 9 : 1));
         off += ((int64_t)R.lx * R.ly + 255) & ~(int64_t)255;
         coff += R.ncx * R.ncy;
     }
@@ -308,8 +330,7 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         fskmc::WindowArgs a;
         a.reps = c->d_reps;
         a.rep_index = r;
-        a.qx = c->qx;
-        a.qy = c->qy;
+        a.geom = fskmc::make_geom(c->qx, c->qy);
         a.colour = win.colour;
         a.w = (uint32_t)w;
         a.h = win.h;
@@ -323,6 +344,56 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         CK(c, fskmc::launch_window(c->model, fp32, a, nactive, c->wpb, c->stream));
     }
     if (pingpong) c->cur ^= 1;
+    return FSKMC_OK;
+}
+
+// Run a schedule (one window list, or one per replica) on the context's
+// engine, starting at window index c->w.
+fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sched, uint64_t seed)
+{
+    const size_t nw = sched[0].size();
+    if (c->engine == FSKMC_ENGINE_PERSISTENT) {
+        std::vector<int8_t> col(sched.size() * nw);
+        std::vector<double> hh(nw);
+        for (size_t r = 0; r < sched.size(); ++r)
+            for (size_t i = 0; i < nw; ++i) col[r * nw + i] = (int8_t)sched[r][i].colour;
+        for (size_t i = 0; i < nw; ++i) hh[i] = sched[0][i].h;
+        fskmc::PersistentRun pr;
+        pr.model = c->model;
+        pr.fp32 = c->clock == FSKMC_CLOCK_FP32;
+        pr.qx = c->qx;
+        pr.qy = c->qy;
+        pr.nrep = c->nrep;
+        pr.reps_host = c->reps.data();
+        pr.reps_dev = c->d_reps;
+        pr.lat = c->d_lat[c->cur];
+        pr.lat2 = c->d_lat[1] ? c->d_lat[1 - c->cur] : nullptr;
+        pr.workload = c->d_workload;
+        pr.counters = c->d_counters;
+        pr.total_cells = c->total_cells;
+        pr.colour = col.data();
+        pr.colour_per_replica = sched.size() > 1;
+        pr.h = hh.data();
+        pr.nwin = (int64_t)nw;
+        pr.w0 = c->w;
+        pr.seed = seed;
+        pr.wpb = std::min(c->wpb, 8);  // the persistent kernel is built for <= 256 threads
+        pr.spin_limit = c->spin_limit;
+        std::string msg;
+        cudaError_t e = fskmc::persistent_run(&c->pers, pr, c->stream, &msg);
+        if (e == cudaErrorTimeout) {
+            c->w += nw;
+            c->windows += nw;
+            return fail(c, FSKMC_ETIMEOUT, "persistent run: %s; the lattice is undefined", msg.c_str());
+        }
+        if (e != cudaSuccess) return fail(c, FSKMC_ECUDA, "persistent run: %s (%s)", cudaGetErrorString(e), msg.c_str());
+        if (c->d_lat[1] && (nw & 1)) c->cur ^= 1;
+    } else {
+        for (size_t i = 0; i < nw; ++i) {
+            fskmc_status st = plain_window(c, sched, i, c->w + i, seed);
+            if (st) return st;
+        }
+    }
     return FSKMC_OK;
 }
 
@@ -507,51 +578,10 @@ fskmc_status fskmc_run(fskmc_ctx *c, fskmc_scheme scheme, double dt, double T, u
     std::vector<std::vector<Win>> sched(per_replica ? c->nrep : 1);
     for (size_t r = 0; r < sched.size(); ++r)
         build_schedule(scheme, n, dt, seed, c->reps[r].rep, c->w, sched[r]);
-    const size_t nw = sched[0].size();
-    if (c->engine == FSKMC_ENGINE_PERSISTENT) {
-        std::vector<int8_t> col(sched.size() * nw);
-        std::vector<double> hh(nw);
-        for (size_t r = 0; r < sched.size(); ++r)
-            for (size_t i = 0; i < nw; ++i) col[r * nw + i] = (int8_t)sched[r][i].colour;
-        for (size_t i = 0; i < nw; ++i) hh[i] = sched[0][i].h;
-        fskmc::PersistentRun pr;
-        pr.model = c->model;
-        pr.fp32 = c->clock == FSKMC_CLOCK_FP32;
-        pr.qx = c->qx;
-        pr.qy = c->qy;
-        pr.nrep = c->nrep;
-        pr.reps_host = c->reps.data();
-        pr.reps_dev = c->d_reps;
-        pr.lat = c->d_lat[c->cur];
-        pr.lat2 = c->d_lat[1] ? c->d_lat[1 - c->cur] : nullptr;
-        pr.workload = c->d_workload;
-        pr.counters = c->d_counters;
-        pr.total_cells = c->total_cells;
-        pr.colour = col.data();
-        pr.colour_per_replica = sched.size() > 1;
-        pr.h = hh.data();
-        pr.nwin = (int64_t)nw;
-        pr.w0 = c->w;
-        pr.seed = seed;
-        pr.wpb = c->wpb;
-        pr.spin_limit = c->spin_limit;
-        std::string msg;
-        cudaError_t e = fskmc::persistent_run(&c->pers, pr, c->stream, &msg);
-        if (e == cudaErrorTimeout) {
-            c->w += nw;
-            c->windows += nw;
-            return fail(c, FSKMC_ETIMEOUT, "persistent run: %s; the lattice is undefined", msg.c_str());
-        }
-        if (e != cudaSuccess) return fail(c, FSKMC_ECUDA, "persistent run: %s (%s)", cudaGetErrorString(e), msg.c_str());
-        if (c->d_lat[1] && (nw & 1)) c->cur ^= 1;
-    } else {
-        for (size_t i = 0; i < nw; ++i) {
-            fskmc_status st = plain_window(c, sched, i, c->w + i, seed);
-            if (st) return st;
-        }
-    }
-    c->w += nw;
-    c->windows += nw;
+    fskmc_status st = exec_windows(c, sched, seed);
+    if (st) return st;
+    c->w += sched[0].size();
+    c->windows += sched[0].size();
     return FSKMC_OK;
 }
 
@@ -561,7 +591,7 @@ fskmc_status fskmc_window(fskmc_ctx *c, int32_t colour, double h, uint64_t seed)
     if (colour != 0 && colour != 1) return fail(c, FSKMC_EINVAL, "colour must be 0 or 1");
     if (!(h > 0.0) || !std::isfinite(h)) return fail(c, FSKMC_EINVAL, "window length must be > 0");
     std::vector<std::vector<Win>> sched(1, std::vector<Win>{{colour, h}});
-    fskmc_status st = plain_window(c, sched, 0, c->w, seed);
+    fskmc_status st = exec_windows(c, sched, seed);
     if (st) return st;
     c->w += 1;
     c->windows += 1;

@@ -18,15 +18,44 @@ struct Replica {
     int64_t lat_off;     // byte offset of the replica's lattice in the lattice buffer
     int32_t cell_off;    // index of the replica's cell 0 in per-cell arrays
     uint32_t rep;        // replica word of the random counters
-    double r[MAX_CLASSES];   // class rates, binary64
-    float rf[MAX_CLASSES];   // the same rates rounded to binary32
+    double r[MAX_CLASSES];       // class rates, binary64
+    uint64_t rq[MAX_CLASSES];    // the rates in fixed point: round(r * 2^qshift)
+    float qscale;                // 2^-qshift (binary32 clock path)
+    int32_t qshift;
 };
+
+// n / d for 0 <= n < 2^16 and 1 <= d <= 2^16 as (n * M) >> 32, M = ceil(2^32 / d).
+struct FastDiv {
+    uint32_t d;
+    uint64_t M;
+};
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    f.M = ((1ull << 32) + d - 1) / d;
+    return f;
+}
+
+// Cell shape and the divisions the window kernel needs.
+struct CellGeom {
+    int32_t qx, qy;
+    FastDiv fqx;  // by qx
+};
+inline CellGeom make_geom(int qx, int qy)
+{
+    CellGeom g;
+    g.qx = qx;
+    g.qy = qy;
+    g.fqx = make_fastdiv((uint32_t)qx);
+    return g;
+}
 
 // Arguments of one fractional window over the active cells of one replica.
 struct WindowArgs {
     const Replica *reps;       // device array
     int32_t rep_index;         // which replica
-    int32_t qx, qy;            // cell shape
+    CellGeom geom;             // cell shape
     int32_t colour;            // 0 = E, 1 = O
     uint32_t w;                // global window index
     double h;                  // window length

@@ -32,7 +32,6 @@ namespace fskmc {
 
 namespace {
 
-constexpr double EDGE_TOL = 1e-12;
 constexpr uint32_t MAX_EVENTS_PER_WINDOW = 1u << 26;
 
 template <int MODEL>
@@ -109,45 +108,6 @@ __device__ __forceinline__ bool slot_owned(int lx, int ly, int d, int qx, int qy
     return (d >= 4) ? (!inside && cross) : (inside || cross);
 }
 
-// binary64 / binary32 clock arithmetic.
-template <typename T>
-struct Clock;
-template <>
-struct Clock<double> {
-    static __device__ __forceinline__ double neglog_ut(uint32_t w0, uint32_t w1)
-    {
-        uint64_t b = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
-        double u = __dmul_rn(__ull2double_rn(b + 1ull), 0x1p-53);
-        return -log(u);
-    }
-    static __device__ __forceinline__ double uc(uint32_t w2)
-    {
-        return __dmul_rn(__dadd_rn(__uint2double_rn(w2), 0.5), 0x1p-32);
-    }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-    static __device__ __forceinline__ double rate(const Replica &R, int k) { return R.r[k]; }
-};
-template <>
-struct Clock<float> {
-    static __device__ __forceinline__ float neglog_ut(uint32_t w0, uint32_t)
-    {
-        float u = __fmul_rn(__uint2float_rn((w0 >> 8) + 1u), 0x1p-24f);
-        return -logf(u);
-    }
-    static __device__ __forceinline__ float uc(uint32_t w2)
-    {
-        return __fmul_rn(__fadd_rn(__uint2float_rn(w2 >> 8), 0.5f), 0x1p-24f);
-    }
-    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-    static __device__ __forceinline__ float rate(const Replica &R, int k) { return R.rf[k]; }
-};
-
 // Position of the r-th (0-based) set bit of m (r < popc(m)).
 __device__ __forceinline__ int select_bit(uint32_t m, int r)
 {
@@ -160,12 +120,23 @@ __device__ __forceinline__ int select_bit(uint32_t m, int r)
     return pos;
 }
 
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
+{
+    return (uint32_t)(((uint64_t)n * f.M) >> 32);
+}
+
+// Bit pattern of a non-negative double: orders like the value.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
 struct Layout {
     int BW, BH, nsite, s, SW;
     int box_bytes, scls_bytes, sitemask_words, slotmask_words;
     int bytes;
 };
 
+// Per-warp shared memory: the cell and its halo (one byte per site), the
+// class code of every own site, membership masks ([mask][word][lane]),
+// then 16 class counts (int), 16 counts as binary64 and 16 fixed-point rates.
 template <int MODEL>
 __host__ __device__ inline Layout make_layout(int qx, int qy)
 {
@@ -174,14 +145,15 @@ __host__ __device__ inline Layout make_layout(int qx, int qy)
     L.BW = qx + 2 * TR::HW;
     L.BH = qy + 2 * TR::HW;
     L.nsite = qx * qy;
-    L.s = (L.nsite + 31) / 32;
-    L.SW = TR::KB ? (8 * L.s + 31) / 32 : 0;
+    L.s = 32;                       // each lane owns one 32-site word of every site mask
+    L.SW = TR::KB ? 8 : 0;          // and 8 words (32 sites x 8 slots) of every slot mask
     L.box_bytes = (L.BW * L.BH + 15) & ~15;
     L.scls_bytes = (L.nsite + 15) & ~15;
     L.sitemask_words = TR::KS * 32;
     L.slotmask_words = TR::KB * L.SW * 32;
     L.bytes = L.box_bytes + L.scls_bytes + 4 * (L.sitemask_words + L.slotmask_words) +
-              4 * MAX_CLASSES;
+              4 * MAX_CLASSES + 8 * MAX_CLASSES + 8 * MAX_CLASSES;
+    L.bytes = (L.bytes + 15) & ~15;
     return L;
 }
 
@@ -217,17 +189,29 @@ __device__ void copy_unwritten(const uint8_t *src, uint8_t *dst, int lx, int ly,
     }
 }
 
-// One cell's fractional window. Returns the number of events; *amb is set
-// if an edge decision landed within EDGE_TOL of the window end.
+// One cell's fractional window (Eqs. totalrate and skeleton run on the cell
+// for the window length). Returns the number of events; *amb is set if an
+// edge decision landed within about 1e-12 (relative) of the window end.
+//
+// CLK = double: the binary64 contract shared with the oracle -- lambda and
+// the class thresholds P_k form the ordered fused multiply-add chain over
+// the counts (as binary64) and the rates; the waiting time is
+// -log(u_t)/lambda; comparisons of non-negative doubles are done on their
+// bit patterns (same order, integer pipe).
+// CLK = float: the rate-class sums are exact 64-bit fixed-point integers
+// (counts times rates rounded to multiples of 2^-qshift), the class is the
+// first k with (w2 * lambda_int) >> 32 < P_k, and only the window clock
+// (lambda, waiting time, tau) is binary32 relative to the window start.
 template <int MODEL, typename CLK, bool PERSIST>
-__device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, int cx, int cy,
+__device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &G, int cx, int cy,
                                 int colour, uint32_t w, double hwin, uint64_t seed,
                                 const uint8_t *src, uint8_t *dst, int lane, bool *amb_out,
                                 bool *bad_out)
 {
     using TR = Traits<MODEL>;
-    using C = Clock<CLK>;
+    constexpr bool F64 = sizeof(CLK) == 8;
     constexpr int K = TR::K, HW = TR::HW, RR = TR::R;
+    const int qx = G.qx, qy = G.qy;
 
     const Layout Lo = make_layout<MODEL>(qx, qy);
     uint8_t *box = wsm;
@@ -235,11 +219,13 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
     uint32_t *sitemask = reinterpret_cast<uint32_t *>(scls + Lo.scls_bytes);
     uint32_t *slotmask = sitemask + Lo.sitemask_words;
     int *cnt = reinterpret_cast<int *>(slotmask + Lo.slotmask_words);
+    double *dcnt = reinterpret_cast<double *>(cnt + MAX_CLASSES);
 
     const int lx = R.lx, ly = R.ly;
     const int m = cy * R.ncx + cx;
     const int X0 = cx * qx, Y0 = cy * qy;
-    const int BW = Lo.BW, BH = Lo.BH, s = Lo.s, SW = Lo.SW, nsite = Lo.nsite;
+    const int BW = Lo.BW, BH = Lo.BH, SW = Lo.SW, nsite = Lo.nsite;
+    const int NL = (nsite + 31) >> 5;  // lanes that own sites
 
     // Stage the cell and its halo (periodic wrap) from the window-start state.
     for (int i = lane; i < BW * BH; i += 32) {
@@ -253,12 +239,12 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
     if (lane < MAX_CLASSES) cnt[lane] = 0;
     __syncwarp();
 
-    // Class build: each lane classifies its own run of sites and slots.
-    const int i0 = lane * s;
-    for (int t = 0; t < s; ++t) {
+    // Class build: each lane classifies its own run of 32 sites and their slots.
+    const int i0 = lane * 32;
+    for (int t = 0; t < 32; ++t) {
         int i = i0 + t;
         if (i >= nsite) break;
-        int llx = i % qx, lly = i / qx;
+        int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
         int p = (lly + HW) * BW + llx + HW;
         int k = site_class<MODEL>(box, BW, p);
         scls[i] = (uint8_t)k;
@@ -290,27 +276,52 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
     }
     __syncwarp();
 
-    // SSA loop (Eqs. totalrate and skeleton on the cell).
-    CLK rk[K];
+    // Per-lane class data: lane k < K holds class k's count and rate.
+    double rk[K];  // binary64 rates (uniform)
 #pragma unroll
-    for (int k = 0; k < K; ++k) rk[k] = C::rate(R, k);
-    const CLK h = (CLK)hwin;
-    CLK tau = (CLK)0;
+    for (int k = 0; k < K; ++k) rk[k] = F64 ? R.r[k] : 0.0;
+    const uint64_t rq_lane = lane < K ? R.rq[lane] : 0ull;
+    const float qscale = R.qscale;
+
+    const long long hbits = dbits(hwin);
+    const float hf = (float)hwin;
+    double tau = 0.0;
+    float tauf = 0.0f;
     bool amb = false;
     uint32_t e = 0;
-    uint32_t rw2 = 0, rw3 = 0;
-    CLK rl = (CLK)0;
+    uint32_t rw3 = 0;
+    double rl = 0.0, ruc = 0.0;
+    float rlf = 0.0f;
+    uint32_t rw2 = 0;
     const uint32_t ctr3 = R.rep | (TAG_EVENT << 24);
 
     for (;;) {
-        CLK P[K];
-        CLK lam = (CLK)0;
+        // Counts of this state, one class per lane.
+        const int n_lane = lane < K ? cnt[lane] : 0;
+        double Pd[K];
+        double lamd = 0.0;
+        uint64_t P_lane = 0, lami = 0;
+        if (F64) {
+            if (lane < K) dcnt[lane] = (double)n_lane;  // one conversion per class, lane-parallel
+            __syncwarp();
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            lam = C::fma((CLK)cnt[k], rk[k], lam);
-            P[k] = lam;
+            for (int k = 0; k < K; ++k) {
+                double nk = dcnt[k];
+                if (dbits(nk) != 0) lamd = __fma_rn(nk, rk[k], lamd);  // fma(0, r, x) == x
+                Pd[k] = lamd;
+            }
+            if (dbits(lamd) == 0) break;
+        } else {
+            // exact integer prefix sums over the classes (lanes 0..15)
+            P_lane = (uint64_t)(uint32_t)n_lane * rq_lane;
+#pragma unroll
+            for (int off = 1; off < 16; off <<= 1) {
+                uint64_t v = __shfl_up_sync(0xffffffffu, P_lane, off);
+                if (lane >= off) P_lane += v;
+            }
+            lami = __shfl_sync(0xffffffffu, P_lane, K - 1);
+            if (lami == 0ull) break;
         }
-        if (lam == (CLK)0) break;
         if (e >= MAX_EVENTS_PER_WINDOW) {  // cannot happen with sane rates; never loop unboundedly
             *bad_out = true;
             break;
@@ -318,32 +329,44 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
         if ((e & 31u) == 0u) {
             // 32 events' draws at once, one Philox block per lane
             u32x4 o = draw(seed, e + (uint32_t)lane, w, (uint32_t)m, ctr3);
-            rl = C::neglog_ut(o.x, o.y);
+            if (F64) {
+                uint64_t b = ((uint64_t)o.x << 21) | (uint64_t)(o.y >> 11);
+                rl = -log(__dmul_rn(__ull2double_rn(b + 1ull), 0x1p-53));
+                ruc = __dmul_rn(__dadd_rn(__uint2double_rn(o.z), 0.5), 0x1p-32);
+            } else {
+                rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
+            }
             rw2 = o.z;
             rw3 = o.w;
         }
         const int src_lane = (int)(e & 31u);
-        const CLK l = __shfl_sync(0xffffffffu, rl, src_lane);
-        const uint32_t w2 = __shfl_sync(0xffffffffu, rw2, src_lane);
         const uint32_t w3 = __shfl_sync(0xffffffffu, rw3, src_lane);
-        const CLK E = C::div(l, lam);
-        const CLK end = C::add(tau, E);
-        if (fabs((double)end - (double)h) < EDGE_TOL * (double)h) amb = true;
-        if (end >= h) break;
-        tau = end;
-
-        const CLK t = C::mul(C::uc(w2), lam);
-        int k = -1;
+        int k;
+        if (F64) {
+            const double l = __shfl_sync(0xffffffffu, rl, src_lane);
+            const double uc = __shfl_sync(0xffffffffu, ruc, src_lane);
+            const double end = __dadd_rn(tau, __ddiv_rn(l, lamd));
+            const long long eb = dbits(end);
+            if (llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+            if (eb >= hbits) break;
+            tau = end;
+            const long long tb = dbits(__dmul_rn(uc, lamd));
+            k = K - 1;
 #pragma unroll
-        for (int kk = K - 1; kk >= 0; --kk)
-            if (t < P[kk]) k = kk;
-        if (k < 0) {  // binary32 only: t rounded up to lambda; take the last non-empty class
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk)
-                if (cnt[kk] > 0 && rk[kk] > (CLK)0) k = kk;
-            if (k < 0) break;
+            for (int kk = K - 2; kk >= 0; --kk)
+                if (tb < dbits(Pd[kk])) k = kk;
+        } else {
+            const float l = __shfl_sync(0xffffffffu, rlf, src_lane);
+            const uint32_t w2 = __shfl_sync(0xffffffffu, rw2, src_lane);
+            const float lamf = __fmul_rn(__ull2float_rn(lami), qscale);
+            const float end = __fadd_rn(tauf, __fdividef(l, lamf));
+            if (end >= hf) break;
+            tauf = end;
+            const uint64_t t = (uint64_t)w2 * (lami >> 32) + (((uint64_t)w2 * (lami & 0xffffffffull)) >> 32);
+            const uint32_t hitc = __ballot_sync(0xffffffffu, lane < K && t < P_lane);
+            k = __ffs(hitc) - 1;
         }
-        const int nk = cnt[k];
+        const int nk = __shfl_sync(0xffffffffu, n_lane, k);
         const uint32_t j = (uint32_t)(((uint64_t)w3 * (uint64_t)(uint32_t)nk) >> 32);
 
         // Rank search: the j-th member of class k in canonical order.
@@ -356,8 +379,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
             c = __popc(sitemask[mk * 32 + lane]);
         }
         int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
+        for (int off = 1; off < NL; off <<= 1) {
             int v = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += v;
         }
@@ -383,82 +405,115 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
         }
         pick = __shfl_sync(0xffffffffu, pick, owner);
         int site, d = 0;
-        if (slot) { site = owner * s + (pick >> 3); d = pick & 7; }
-        else { site = owner * s + pick; }
-        const int slx = site % qx, sly = site / qx;
-        const int p = (sly + HW) * BW + slx + HW;
-        int po = p, pt = p;
+        if (slot) { site = owner * 32 + (pick >> 3); d = pick & 7; }
+        else { site = owner * 32 + pick; }
+        const int sy = (int)fdiv((uint32_t)site, G.fqx), sx = site - sy * qx;
+        int ox = sx, oy = sy, tx = sx, ty = sy;
         if (slot) {
             int dir = d & 3;
-            int pn = p + dir_dy(dir) * BW + dir_dx(dir);
-            if (d < 4) pt = pn; else po = pn;
+            if (d < 4) { tx += dir_dx(dir); ty += dir_dy(dir); }
+            else { ox += dir_dx(dir); oy += dir_dy(dir); }
         }
-        // Apply the event (the update sigma -> sigma^{x,omega}).
-        if (lane == 0) {
-            if (MODEL == ADSDES || MODEL == ISING) {
-                box[p] ^= 1;
-            } else if (MODEL == DIFFUSION) {
-                if (k < 10) box[p] ^= 1;
-                else { box[po] = 0; box[pt] = 1; }
-            } else {
-                if (k == 0) box[p] = 1;
-                else if (k == 3) box[p] = 0;
-                else if (k == 1) { box[po] = 2; box[pt] = 2; }
-                else { box[po] = 0; box[pt] = 0; }
-            }
-        }
-        __syncwarp();
-
-        // Refresh the classes of every site within RR of the changed sites,
-        // one site per lane.
-        {
-            int ox = (po % BW) - HW, oy = (po / BW) - HW;
-            int tx = (pt % BW) - HW, ty = (pt / BW) - HW;
-            int x0 = min(ox, tx) - RR, x1 = max(ox, tx) + RR;
-            int y0 = min(oy, ty) - RR, y1 = max(oy, ty) + RR;
-            int rw = x1 - x0 + 1;
-            int ux = x0 + lane % rw, uy = y0 + lane / rw;
-            if (lane < rw * (y1 - y0 + 1) && ux >= 0 && ux < qx && uy >= 0 && uy < qy) {
-                int i = uy * qx + ux;
-                int own = i / s, tt = i - own * s;
-                int pu = (uy + HW) * BW + ux + HW;
-                int knew = site_class<MODEL>(box, BW, pu);
-                int kold = (int8_t)scls[i];
-                if (knew != kold) {
+        const int po = (oy + HW) * BW + ox + HW, pt = (ty + HW) * BW + tx + HW;
+        if (MODEL == ADSDES || MODEL == ISING) {
+            // Spin flip at (sx, sy): its class k = 5 sigma + n becomes k -+ 5,
+            // and each neighbour inside the cell changes n by +-1. The new
+            // classes follow from the old ones; no lattice reads needed.
+            const int sold = k >= 5;
+            if (lane == 0) box[po] = (uint8_t)(1 - sold);
+            if (lane < 5) {
+                int ux = sx, uy = sy;
+                if (lane > 0) { ux += dir_dx(lane - 1); uy += dir_dy(lane - 1); }
+                if (ux >= 0 && ux < qx && uy >= 0 && uy < qy) {
+                    const int i = uy * qx + ux;
+                    int kold, knew;
+                    if (lane == 0) { kold = k; knew = sold ? k - 5 : k + 5; }
+                    else { kold = (int8_t)scls[i]; knew = kold + (sold ? -1 : 1); }
                     scls[i] = (uint8_t)knew;
-                    uint32_t bit = 1u << tt;
-                    if (kold >= 0) {
-                        atomicAnd(&sitemask[mask_of<MODEL>(kold) * 32 + own], ~bit);
-                        atomicSub(&cnt[kold], 1);
-                    }
-                    if (knew >= 0) {
-                        atomicOr(&sitemask[mask_of<MODEL>(knew) * 32 + own], bit);
-                        atomicAdd(&cnt[knew], 1);
-                    }
+                    const int own = i >> 5;
+                    const uint32_t bit = 1u << (i & 31);
+                    atomicAnd(&sitemask[kold * 32 + own], ~bit);
+                    atomicOr(&sitemask[knew * 32 + own], bit);
+                    atomicSub(&cnt[kold], 1);
+                    atomicAdd(&cnt[knew], 1);
                 }
-                if (TR::KB) {
-#pragma unroll
-                    for (int dd = 0; dd < 8; ++dd) {
-                        if (!slot_owned(ux, uy, dd, qx, qy, colour)) continue;
-                        int dir = dd & 3;
-                        int pn = pu + dir_dy(dir) * BW + dir_dx(dir);
-                        int kn = (dd < 4) ? slot_class<MODEL>(box, BW, pu, pn)
-                                          : slot_class<MODEL>(box, BW, pn, pu);
-                        int bitpos = tt * 8 + dd;
-                        int wofs = (bitpos >> 5) * 32 + own;
-                        uint32_t bit = 1u << (bitpos & 31);
-                        int ko = -1;
-#pragma unroll
-                        for (int mb = 0; mb < TR::KB; ++mb)
-                            if (slotmask[mb * SW * 32 + wofs] & bit) ko = slot_class_of_mask<MODEL>(mb);
-                        if (kn == ko) continue;
-                        if (ko >= 0) {
-                            atomicAnd(&slotmask[mask_of<MODEL>(ko) * SW * 32 + wofs], ~bit);
-                            atomicSub(&cnt[ko], 1);
+            }
+        } else {
+            // Apply the event (the update sigma -> sigma^{x,omega}).
+            if (lane == 0) {
+                if (MODEL == ADSDES || MODEL == ISING) {
+                    box[po] ^= 1;
+                } else if (MODEL == DIFFUSION) {
+                    if (k < 10) box[po] ^= 1;
+                    else { box[po] = 0; box[pt] = 1; }
+                } else {
+                    if (k == 0) box[po] = 1;
+                    else if (k == 3) box[po] = 0;
+                    else if (k == 1) { box[po] = 2; box[pt] = 2; }
+                    else { box[po] = 0; box[pt] = 0; }
+                }
+            }
+            __syncwarp();
+
+            // Refresh the classes of every own site within RR of the changed
+            // sites, one site per lane (fixed region widths: 4 for RR = 1; 6 or
+            // 5 for RR = 2 depending on the pair's orientation).
+            {
+                const int x0 = min(ox, tx) - RR, y0 = min(oy, ty) - RR;
+                const int x1 = max(ox, tx) + RR, y1 = max(oy, ty) + RR;
+                int ux, uy;
+                if (RR == 1) {
+                    ux = x0 + (lane & 3);
+                    uy = y0 + (lane >> 2);
+                } else if (oy != ty) {
+                    ux = x0 + lane % 5;
+                    uy = y0 + lane / 5;
+                } else {
+                    ux = x0 + lane % 6;
+                    uy = y0 + lane / 6;
+                }
+                if (ux <= x1 && uy <= y1 && ux >= 0 && ux < qx && uy >= 0 && uy < qy) {
+                    const int i = uy * qx + ux;
+                    const int own = i >> 5, tt = i & 31;
+                    const int pu = (uy + HW) * BW + ux + HW;
+                    const int knew = site_class<MODEL>(box, BW, pu);
+                    const int kold = (int8_t)scls[i];
+                    if (knew != kold) {
+                        scls[i] = (uint8_t)knew;
+                        const uint32_t bit = 1u << tt;
+                        if (kold >= 0) {
+                            atomicAnd(&sitemask[mask_of<MODEL>(kold) * 32 + own], ~bit);
+                            atomicSub(&cnt[kold], 1);
                         }
-                        if (kn >= 0) {
-                            atomicOr(&slotmask[mask_of<MODEL>(kn) * SW * 32 + wofs], bit);
-                            atomicAdd(&cnt[kn], 1);
+                        if (knew >= 0) {
+                            atomicOr(&sitemask[mask_of<MODEL>(knew) * 32 + own], bit);
+                            atomicAdd(&cnt[knew], 1);
+                        }
+                    }
+                    if (TR::KB) {
+    #pragma unroll
+                        for (int dd = 0; dd < 8; ++dd) {
+                            if (!slot_owned(ux, uy, dd, qx, qy, colour)) continue;
+                            const int dir = dd & 3;
+                            const int pn = pu + dir_dy(dir) * BW + dir_dx(dir);
+                            const int kn = (dd < 4) ? slot_class<MODEL>(box, BW, pu, pn)
+                                                    : slot_class<MODEL>(box, BW, pn, pu);
+                            const int bitpos = tt * 8 + dd;
+                            const int wofs = (bitpos >> 5) * 32 + own;
+                            const uint32_t bit = 1u << (bitpos & 31);
+                            int ko = -1;
+    #pragma unroll
+                            for (int mb = 0; mb < TR::KB; ++mb)
+                                if (slotmask[mb * SW * 32 + wofs] & bit) ko = slot_class_of_mask<MODEL>(mb);
+                            if (kn == ko) continue;
+                            if (ko >= 0) {
+                                atomicAnd(&slotmask[mask_of<MODEL>(ko) * SW * 32 + wofs], ~bit);
+                                atomicSub(&cnt[ko], 1);
+                            }
+                            if (kn >= 0) {
+                                atomicOr(&slotmask[mask_of<MODEL>(kn) * SW * 32 + wofs], bit);
+                                atomicAdd(&cnt[kn], 1);
+                            }
                         }
                     }
                 }
@@ -471,7 +526,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, int qx, int qy, 
     // Write back the write set: own sites, plus the halo ends of owned cross
     // bonds for the two-site models (columns in E windows, rows in O windows).
     for (int i = lane; i < nsite; i += 32) {
-        int llx = i % qx, lly = i / qx;
+        int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
         dst[(int64_t)(Y0 + lly) * lx + X0 + llx] = box[(lly + HW) * BW + llx + HW];
     }
     if (TR::KB) {
@@ -515,12 +570,12 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
         // right of an E cell, below an O cell
         int ncx2 = a.colour == 0 ? (cx + 1) % R.ncx : cx;
         int ncy2 = a.colour == 0 ? cy : (cy + 1) % R.ncy;
-        copy_unwritten<false>(src, dst, R.lx, R.ly, a.qx, a.qy, ncx2, ncy2, a.colour, lane);
+        copy_unwritten<false>(src, dst, R.lx, R.ly, a.geom.qx, a.geom.qy, ncx2, ncy2, a.colour, lane);
     }
     bool amb = false, bad = false;
-    uint32_t e = cell_window<MODEL, CLK, false>(smem + (size_t)wib * smem_per_warp, R, a.qx, a.qy,
-                                                cx, cy, a.colour, a.w, a.h, a.seed, src, dst,
-                                                lane, &amb, &bad);
+    uint32_t e = cell_window<MODEL, CLK, false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cx,
+                                                cy, a.colour, a.w, a.h, a.seed, src, dst, lane,
+                                                &amb, &bad);
     if (lane == 0) {
         a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
         atomicAdd(&a.counters[0], (unsigned long long)e);
@@ -530,24 +585,27 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
 }
 
 // ---------------------------------------------------------------------------
-// Persistent engine. Tasks are (window i, replica r, cell m) for every cell,
-// active or not, dequeued from one global counter in the order: window-major;
-// within a window all active cells (every replica) before all inactive ones.
-// A task waits only on tasks that precede it in that order, so a dequeued
-// task's prerequisites are always held by running warps.
-//   epoch[m] = i + 1 once every write to, and read of, cell m's sites for
-//   windows <= i is complete.
-//   Active (m, i): needs epoch >= i on m and its 4 edge neighbours (in place)
-//   or its 3x3 neighbourhood (ping-pong), then runs the window.
-//   Inactive (m, i): in ping-pong mode waits on its 3x3 neighbourhood and
-//   copies its unwritten sites; then waits until its 4 active edge
-//   neighbours (the only cells that write into it) reach epoch i + 1.
+// Persistent engine. One launch runs every window of every replica; tasks
+// are dequeued from one global counter, window-major, and a task waits only
+// on tasks that precede it in that order, so a dequeued task's prerequisites
+// are always held by running warps.
+// In-place models (spin flip, ZGB): tasks are the active cells only.
+//   epoch[m] = 1 + the last window in which cell m was active. Active (m, i)
+//   needs epoch[m] >= 1 + (m's previous active window) and, for each edge
+//   neighbour n, epoch[n] >= 1 + (n's last active window before i): then no
+//   site m reads or writes is being written or read by anyone else.
+// Ping-pong model (diffusion): every cell has a task in every window, active
+//   cells first. epoch[m] = i + 1 once every read and write of m's sites for
+//   windows <= i is done. Active (m, i) waits on its 3x3 neighbourhood at
+//   epoch >= i; inactive (m, i) does the same, copies its unwritten sites,
+//   then waits until its 4 active edge neighbours reach epoch i + 1.
 // Every wait polls at most spin_limit times; on expiry the warp raises the
 // abort flag, counts a timeout and the whole launch drains.
 // ---------------------------------------------------------------------------
 struct PParams {
     const Replica *reps;
-    int32_t nrep, qx, qy;
+    int32_t nrep;
+    CellGeom geom;
     uint8_t *lat, *lat2;
     int32_t *workload;
     unsigned long long *counters;
@@ -555,6 +613,8 @@ struct PParams {
     int32_t total_cells, total_active;
     const int8_t *colour;
     int32_t colour_per_replica;
+    const int2 *prev;          // per (replica,) window: last earlier window of the same / other colour
+    int32_t inplace;           // in-place models: only active cells have tasks
     const double *h;
     int64_t nwin;
     uint32_t w0;
@@ -574,7 +634,7 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p)
 // Lanes 0..nd-1 poll deps[lane] until epoch >= target. Returns false on
 // timeout or abort.
 __device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target,
-                            const PParams &P, int lane)
+                            const PParams &P, int lane)  // target may differ per lane
 {
     uint32_t spins = 0;
     for (;;) {
@@ -603,12 +663,14 @@ template <int MODEL, typename CLK>
 __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    const PParams P = *pp;
+    const PParams &P = *pp;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint8_t *wsm = smem + (size_t)wib * smem_per_warp;
     const bool pingpong = P.lat2 != nullptr;
-    const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)P.total_cells;
+    const bool inplace = P.inplace != 0;
+    const int per_window = inplace ? P.total_active : P.total_cells;
+    const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)per_window;
 
     for (;;) {
         unsigned long long t = 0;
@@ -618,8 +680,8 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         int ab = 0;
         if (lane == 0) ab = *(volatile int32_t *)P.abort_flag;
         if (__shfl_sync(0xffffffffu, ab, 0)) break;
-        const int i = (int)(t / (unsigned long long)P.total_cells);
-        const int u = (int)(t % (unsigned long long)P.total_cells);
+        const int i = (int)(t / (unsigned long long)per_window);
+        const int u = (int)(t % (unsigned long long)per_window);
         const bool active = u < P.total_active;
         const int a = active ? u : u - P.total_active;
         int lo = 0, hi = P.nrep;  // last r with act_prefix[r] <= a
@@ -630,7 +692,8 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         const int r = lo;
         const int k = a - P.act_prefix[r];
         const Replica &R = P.reps[r];
-        const int wcol = P.colour[P.colour_per_replica ? (int64_t)r * P.nwin + i : i];
+        const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
+        const int wcol = P.colour[widx];
         const int ccol = active ? wcol : 1 - wcol;
         const int half = R.ncx >> 1;
         const int cy = k / half;
@@ -642,27 +705,30 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         cur += R.lat_off;
         nxt += R.lat_off;
 
-        // dependency of this lane: 3x3 neighbourhood (lanes 0..8) or
-        // self + 4 edge neighbours (lanes 0..4)
-        int ddx = 0, ddy = 0;
-        bool has = false;
-        if (pingpong) {
-            has = lane < 9;
-            ddx = lane % 3 - 1;
-            ddy = lane / 3 - 1;
-        } else {
-            has = lane < 5;
-            ddx = lane == 1 ? 1 : (lane == 3 ? -1 : 0);
-            ddy = lane == 2 ? 1 : (lane == 4 ? -1 : 0);
-        }
-        const int dcx = (cx + ddx + R.ncx) % R.ncx, dcy = (cy + ddy + R.ncy) % R.ncy;
-        const int dep = dcy * R.ncx + dcx;
         bool ok = true;
-        if (active || pingpong) ok = wait_epochs(ep, dep, has, i, P, lane);
+        if (inplace) {
+            // epoch[c] = 1 + the last window in which cell c was active.
+            // Lane 0: this cell's previous active window; lanes 1..4: the
+            // edge neighbours' last active window before this one.
+            const int2 pv = P.prev[widx];
+            const int ex = lane == 1 ? 1 : (lane == 3 ? -1 : 0);
+            const int ey = lane == 2 ? 1 : (lane == 4 ? -1 : 0);
+            const int dcx = (cx + ex + R.ncx) % R.ncx, dcy = (cy + ey + R.ncy) % R.ncy;
+            const int target = (lane == 0 ? pv.x : pv.y) + 1;
+            ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 5 && target > 0, target, P, lane);
+        } else {
+            // ping-pong: every cell has a task in every window and
+            // epoch[c] = 1 + the last window whose reads and writes of cell
+            // c's sites are complete; active cells wait on their 3x3
+            // neighbourhood
+            const int ddx = lane % 3 - 1, ddy = lane / 3 - 1;
+            const int dcx = (cx + ddx + R.ncx) % R.ncx, dcy = (cy + ddy + R.ncy) % R.ncy;
+            ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 9, i, P, lane);
+        }
         if (!ok) break;
         if (active) {
             bool amb = false, bad = false;
-            uint32_t e = cell_window<MODEL, CLK, true>(wsm, R, P.qx, P.qy, cx, cy, ccol,
+            uint32_t e = cell_window<MODEL, CLK, true>(wsm, R, P.geom, cx, cy, ccol,
                                                       P.w0 + (uint32_t)i, P.h[i], P.seed, cur,
                                                       nxt, lane, &amb, &bad);
             if (lane == 0) {
@@ -672,7 +738,7 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
                 if (bad) atomicAdd(&P.counters[3], 1ull);
             }
         } else {
-            if (pingpong) copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.qx, P.qy, cx, cy, wcol, lane);
+            copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.geom.qx, P.geom.qy, cx, cy, wcol, lane);
             // the active edge neighbours write into this cell: wait for them
             int ex = lane == 0 ? 1 : (lane == 1 ? -1 : 0);
             int ey = lane == 2 ? 1 : (lane == 3 ? -1 : 0);
@@ -688,10 +754,11 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         }
     }
 }
+
 template <int MODEL>
 cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
 {
-    const int spw = make_layout<MODEL>(a.qx, a.qy).bytes;
+    const int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
     size_t smem = (size_t)spw * wpb;
     int blocks = (nactive + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
@@ -759,6 +826,8 @@ struct PersistentState {
     int32_t *d_prefix = nullptr;
     int8_t *d_colour = nullptr;
     size_t colour_cap = 0;
+    int2 *d_prev = nullptr;
+    size_t prev_cap = 0;
     double *d_h = nullptr;
     size_t h_cap = 0;
     int32_t total_cells = 0;
@@ -777,6 +846,7 @@ void persistent_free(PersistentState *st)
     cudaFree(st->d_queue);
     cudaFree(st->d_prefix);
     cudaFree(st->d_colour);
+    cudaFree(st->d_prev);
     cudaFree(st->d_h);
     cudaFreeHost(st->h_abort);
     delete st;
@@ -851,13 +921,30 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         PCK(cudaMalloc(&st->d_h, sizeof(double) * (size_t)run.nwin));
         st->h_cap = (size_t)run.nwin;
     }
+    // last earlier window of the same and of the other colour, per window
+    std::vector<int2> prev(ncol);
+    const int nsched = run.colour_per_replica ? run.nrep : 1;
+    for (int r = 0; r < nsched; ++r) {
+        int last[2] = {-1, -1};
+        for (int64_t i = 0; i < run.nwin; ++i) {
+            const int c = run.colour[(size_t)r * run.nwin + i];
+            prev[(size_t)r * run.nwin + i] = make_int2(last[c], last[1 - c]);
+            last[c] = (int)i;
+        }
+    }
+    if (ncol > st->prev_cap) {
+        cudaFree(st->d_prev);
+        st->d_prev = nullptr;
+        PCK(cudaMalloc(&st->d_prev, sizeof(int2) * ncol));
+        st->prev_cap = ncol;
+    }
+    PCK(cudaMemcpyAsync(st->d_prev, prev.data(), sizeof(int2) * ncol, cudaMemcpyHostToDevice, s));
     PCK(cudaMemcpyAsync(st->d_colour, run.colour, ncol, cudaMemcpyHostToDevice, s));
     PCK(cudaMemcpyAsync(st->d_h, run.h, sizeof(double) * (size_t)run.nwin, cudaMemcpyHostToDevice, s));
     PParams P;
     P.reps = run.reps_dev;
     P.nrep = run.nrep;
-    P.qx = run.qx;
-    P.qy = run.qy;
+    P.geom = make_geom(run.qx, run.qy);
     P.lat = run.lat;
     P.lat2 = run.lat2;
     P.workload = run.workload;
@@ -867,6 +954,8 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     P.total_active = run.total_cells / 2;
     P.colour = st->d_colour;
     P.colour_per_replica = run.colour_per_replica ? 1 : 0;
+    P.prev = st->d_prev;
+    P.inplace = run.lat2 == nullptr ? 1 : 0;
     P.h = st->d_h;
     P.nwin = run.nwin;
     P.w0 = (uint32_t)run.w0;

@@ -1,0 +1,88 @@
+"""Parity at the benchmark workloads' full sizes, in the launch
+configurations the benchmark uses, on sampled cells the oracle computes one
+by one (same seeded inputs on both sides)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1105_4673_gb300 as F
+from workloads import WORKLOADS, ensemble_replicas, random_lattice
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1105_4673_gb300 import build
+    build.build()
+
+
+def _sample_cells(ncx, ncy, colour, n, seed):
+    rng = np.random.default_rng(seed)
+    cells = []
+    while len(cells) < n:
+        m = int(rng.integers(0, ncx * ncy))
+        if ((m % ncx) + (m // ncx)) % 2 == colour and m not in cells:
+            cells.append(m)
+    # always include the wrap-around corners
+    for m in (0, ncx - 1, ncx * (ncy - 1), ncx * ncy - 1):
+        if ((m % ncx) + (m // ncx)) % 2 == colour and m not in cells:
+            cells.append(m)
+    return cells
+
+
+@pytest.mark.parametrize("name,nstates,p,colour,engine", [
+    ("ising1024", 2, None, 0, "PLAIN"),
+    ("ising1024", 2, None, 1, "PERSISTENT"),
+    ("diffusion4096", 2, [0.7, 0.3], 1, "PLAIN"),
+    ("zgb16384", 3, [0.8, 0.1, 0.1], 0, "PLAIN"),
+])
+def test_fullsize_window_sampled(name, nstates, p, colour, engine):
+    w = WORKLOADS[name]
+    lx, ly, (qx, qy) = w["lx"], w["ly"], w["q"]
+    lat = random_lattice(lx, ly, nstates, w["seed"], p=p)
+    h = w["dt"] if w["scheme"] != "STRANG" else w["dt"] / 2
+    widx = 12345
+    seed = w["seed"]
+    with F.Context(lx, ly, w["model"], w["rates"], w["q"]) as c:
+        c.set_state(lat)
+        c.window_index = widx
+        if engine == "PLAIN":
+            c.window(colour, h, seed)
+        else:  # one-window persistent run through the schedule of a single window
+            c.set_engine("PERSISTENT")
+            c.window(colour, h, seed)
+        got = c.get_state()
+        wl = c.workload()
+        assert c.stats()["check_failures"] == 0
+    ncx, ncy = lx // qx, ly // qy
+    cells = _sample_cells(ncx, ncy, colour, 24, 7)
+    ref, ev, amb = oracle.window_cells(lx, ly, qx, qy, w["model"], w["rates"], lat, colour, h,
+                                       widx, seed, cells)
+    for m, e, a in zip(cells, ev, amb):
+        ws = oracle.cell_writeset(lx, ly, qx, qy, w["model"], m, colour)
+        if a:
+            continue
+        assert np.array_equal(got[ws], ref[ws]), f"cell {m}"
+        assert wl[m] == e, f"cell {m} events"
+
+
+def test_fullsize_ensemble_sampled_replicas():
+    """The 512-replica ensemble in one persistent launch (binary64 clocks);
+    replicas sampled across sizes checked against the oracle."""
+    w = WORKLOADS["ensemble512"]
+    reps = ensemble_replicas(w.get("n", 512), w["seed"])
+    seed = w["seed"]
+    with F.Context(model=w["model"], q=(16, 16), batch=reps) as b:
+        b.set_engine("PERSISTENT")
+        b.init_random(seed, w["coverage"])
+        b.run(w["scheme"], w["dt"], 0.4, seed)
+        assert b.stats()["check_failures"] == 0
+        picks = [r for r in range(len(reps)) if reps[r]["lx"] <= 128][:6]
+        for r in picks:
+            rp = reps[r]
+            init = oracle.init_bernoulli(rp["lx"], rp["ly"], seed, w["coverage"], replica=r)
+            orc = oracle.FSRun(rp["lx"], rp["ly"], 16, 16, w["model"], rp["rates"], init, replica=r)
+            orc.run(w["scheme"], w["dt"], 0.4, seed)
+            if orc.ambiguous == 0:
+                assert np.array_equal(b.get_state(r), orc.lat), f"replica {r}"

@@ -48,6 +48,14 @@ def ensemble_replicas(n: int = 512, seed: int = SEED_BASE + 3):
 
 
 def random_lattice(lx: int, ly: int, nstates: int, seed: int, p=None) -> np.ndarray:
-    """A seeded random lattice (uint8, row-major) for parity cases."""
+    """A seeded random lattice (uint8, row-major) for parity cases: state s
+    with probability p[s] (uniform if None), probabilities rounded to
+    multiples of 1/256 so that full-size lattices need no wide temporaries."""
     rng = np.random.default_rng(seed)
-    return rng.choice(nstates, size=lx * ly, p=p).astype(np.uint8)
+    p = np.full(nstates, 1.0 / nstates) if p is None else np.asarray(p, float)
+    cut = np.round(np.cumsum(p) * 256).astype(np.int64)[:-1]
+    u = rng.integers(0, 256, size=lx * ly, dtype=np.uint8)
+    out = np.zeros(lx * ly, np.uint8)
+    for c in cut:
+        out += (u >= c).astype(np.uint8)
+    return out
