@@ -108,20 +108,15 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        return {}
-
-
-# Algorithmic work of one event of the spin-flip models on the warp-per-cell
-# design (lane-operations, integer or floating point): one Philox4x32-10
-# block (10 rounds x 8 ops + 9 key bumps x 2), the waiting time (1 log + 1
-# divide, ~30), the class threshold chain (2 ops x 10 classes), the rank
-# search over 32 lanes (popcount + 5-step scan + ballot/select, ~12 ops per
-# lane) and the class refresh of the 5 sites a flip touches (~15 ops each).
-OPS_PER_EVENT = 98 + 30 + 20 + 12 * 32 + 5 * 15
+# Roofline of the binary64 window kernel: it is bound by the FP64 pipe
+# (ncu: ~82% of its peak). Algorithmic binary64 operations per event of the
+# contract, each a warp-uniform instruction of the cell's warp: the ordered
+# fused multiply-add chain over the 10 Ising classes, the divide, the
+# threshold multiply, the clock add and the logarithm.
+FP64_OPS_PER_EVENT = 10 + 4
+# Peak: the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp instructions,
+# 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
+FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
 
 
 def cpu_baseline(w, seconds):
@@ -262,13 +257,10 @@ def main():
     if rank != 0:
         ctx.close()
         return
-    pk = peaks()
     cs = clk.summary()
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # Gop/s, INT32/FP32 lanes at max clock
     k_events_per_launch = events / max(len(kernel_ms), 1)
     k_avg_s = float(np.mean(kernel_ms)) / 1000.0
-    achieved = k_events_per_launch * OPS_PER_EVENT / k_avg_s / 1e9
+    achieved = k_events_per_launch * FP64_OPS_PER_EVENT / k_avg_s / 1e9
     cb = cpu_baseline(w, args.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
@@ -279,12 +271,15 @@ def main():
                                f"{w['rates'].get('betaJ')} q={w['q'][0]} {w['scheme']} dt={w['dt']}",
                    "step": f"{STEP_T:g} time units ({len(col)} windows) + observables",
                    "clock": "fp64", "engine": "plain", "l2": "flushed between timed steps"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_WARP_OPS_PEAK_G,
+                     "unit": "G fp64 warp-ops/s", "frac": achieved / FP64_WARP_OPS_PEAK_G,
+                     "traffic": None,
                      "kernel": "fs_window_kernel<ISING,double>",
                      "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
-                     "ops_per_event": OPS_PER_EVENT,
-                     "peak_note": "152 SMs x 128 INT32/FP32 lanes x max SM clock (derived)"},
+                     "events_per_launch": k_events_per_launch,
+                     "fp64_ops_per_event": FP64_OPS_PER_EVENT,
+                     "peak_note": "derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA; "
+                                  "HBM is not the bound (2.27 B/site/window)"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
                 "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
@@ -298,9 +293,14 @@ def main():
 
 def measure_variants(F, w, stream, seed, steps):
     """The same workload through the persistent engine (one graph-launched
-    kernel per run) with binary64 and binary32 window clocks."""
+    kernel per run) with binary64 and binary32 window clocks; the 512-replica
+    ensemble in one persistent launch per run (binary32 clock, the batched
+    form); and the binary32-vs-binary64 difference of the observables."""
     import torch
     res = {}
+    res["ensemble512_persistent_fp32"] = ensemble_rate(F, stream, "FP32")
+    res["ensemble512_persistent_fp64"] = ensemble_rate(F, stream, "FP64")
+    res["fp32_vs_fp64"] = clock_error(F, stream, w)
     for engine, clock in (("PERSISTENT", "FP64"), ("PERSISTENT", "FP32"), ("PLAIN", "FP32")):
         c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream)
         c.set_engine(engine)
@@ -320,6 +320,74 @@ def measure_variants(F, w, stream, seed, steps):
                                                     "events": ev}
         c.close()
     return res
+
+
+def ensemble_rate(F, stream, clock, T=5.0):
+    """Events/s of the 512-replica ensemble (sides 64..512, betaJ in
+    [0.2, 0.8], ka/kd log-uniform) advanced by T in one persistent run."""
+    import torch
+    from workloads import ensemble_replicas
+    w = WORKLOADS["ensemble512"]
+    reps = ensemble_replicas(w["n"], w["seed"])
+    q, wpb, _ = F.autotune(reps, w["model"], w["scheme"], w["dt"], clock=clock,
+                           engine="PERSISTENT", coverage=w["coverage"], seed=w["seed"],
+                           stream=stream)
+    b = F.Context(model=w["model"], q=q, batch=reps, stream=stream)
+    b.set_engine("PERSISTENT")
+    b.set_warps_per_block(wpb)
+    b.set_clock(clock)
+    b.init_random(w["seed"], w["coverage"])
+    b.run(w["scheme"], w["dt"], 1.0, w["seed"])
+    torch.cuda.synchronize()
+    e0 = b.stats()["events"]
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    b.run(w["scheme"], w["dt"], T, w["seed"])
+    c.record(stream)
+    torch.cuda.synchronize()
+    ev = b.stats()["events"] - e0
+    out = {"events_per_s": ev / (a.elapsed_time(c) / 1000), "events": ev, "replicas": len(reps),
+           "sites": int(sum(r["lx"] * r["ly"] for r in reps)), "T": T, "cells": b.info()["cells"],
+           "autotuned": {"q": q[0], "warps_per_block": wpb}}
+    b.close()
+    return out
+
+
+def clock_error(F, stream, w, n=64, L=128, T=10.0):
+    """Binary32 minus binary64 clock, per observable, over n independent
+    replicas of an L x L lattice of the workload's model (mean difference and
+    its standard error), and each form's dt-error estimate against dt/16."""
+    import torch
+    reps = [dict(lx=L, ly=L, rates=w["rates"]) for _ in range(n)]
+
+    def run(clock, dt, seed):
+        b = F.Context(model=w["model"], q=w["q"], batch=reps, stream=stream)
+        b.set_engine("PERSISTENT")
+        b.set_clock(clock)
+        b.init_random(seed, w.get("coverage", 0.5))
+        b.run(w["scheme"], dt, T, seed)
+        obs = []
+        for r in range(n):
+            cov, en, _ = b.observables(r, 1)
+            obs.append([cov[1], en])
+        obs = np.array(obs)
+        b.close()
+        return obs
+
+    out = {"replicas": n, "lattice": f"{L}x{L}", "T": T, "dt": w["dt"]}
+    f64 = run("FP64", w["dt"], 101)
+    f32 = run("FP32", w["dt"], 202)
+    ref = run("FP64", w["dt"] / 16, 303)
+    for j, name in enumerate(("coverage", "energy")):
+        d = f32[:, j].mean() - f64[:, j].mean()
+        se = float(np.sqrt(f32[:, j].var(ddof=1) / n + f64[:, j].var(ddof=1) / n))
+        e64 = f64[:, j].mean() - ref[:, j].mean()
+        e32 = f32[:, j].mean() - ref[:, j].mean()
+        se_r = float(np.sqrt(f64[:, j].var(ddof=1) / n + ref[:, j].var(ddof=1) / n))
+        out[name] = {"fp32_minus_fp64": float(d), "se": se, "within_3se": bool(abs(d) < 3 * se),
+                     "dt_error_fp64": float(e64), "dt_error_fp32": float(e32), "dt_error_se": se_r}
+    torch.cuda.synchronize()
+    return out
 
 
 def schedule(w, T):

@@ -146,8 +146,9 @@ fskmc_status fskmc_set_engine(fskmc_ctx *ctx, fskmc_engine engine);
 fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
 
 /* Persistent engine: how many times a cell polls a neighbour's progress
-   before giving up (default 2^24, about a second or more). A run whose wait
-   gives up returns FSKMC_ETIMEOUT and leaves the lattice undefined. */
+   before giving up (default 2^20; polls back off to one per 4 us, so about
+   4 s). A run whose wait gives up returns FSKMC_ETIMEOUT and leaves the
+   lattice undefined. */
 fskmc_status fskmc_set_spin_limit(fskmc_ctx *ctx, uint32_t polls);
 
 /* Effective cell shape and sizes: out[0]=qx, out[1]=qy, out[2]=replicas,
@@ -228,6 +229,24 @@ fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);
 
 /* Wait until all work queued on the context's stream has finished. */
 fskmc_status fskmc_sync(fskmc_ctx *ctx);
+
+/*
+ * Autotuner for the batched workload: for every square cell size q in
+ * {8, 16, 32} that all n lattices admit and warps per block in {2, 4, 8},
+ * builds a scratch batch context (lattices[n], rates[n], model; Bernoulli
+ * (coverage) start from seed), runs one warm-up step and times 4 steps of
+ * `scheme` with window dt on the given engine and clock (CUDA events on
+ * `stream`). Returns the fastest cell shape and warps per block, and its
+ * events/s in *best_rate (may be NULL). The cell shape changes the
+ * decomposition, hence the approximation (finer Trotter error at larger q,
+ * Section 4); warps per block never change results. Errors are reported
+ * through fskmc_last_error(NULL). EINVAL: NULL outputs, dt <= 0, no q fits.
+ */
+fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_model model,
+                            const fskmc_rates *rates, fskmc_scheme scheme, double dt,
+                            fskmc_clock clock, fskmc_engine engine, double coverage,
+                            uint64_t seed, void *stream, fskmc_cell_shape *best_cell,
+                            int32_t *best_wpb, double *best_rate);
 
 /*
  * Observables of a lattice already in device memory, computed without

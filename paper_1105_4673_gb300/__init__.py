@@ -35,7 +35,7 @@ EXPORTS = [
     "fskmc_set_spin_limit", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
-    "fskmc_observables_noalloc",
+    "fskmc_observables_noalloc", "fskmc_autotune",
 ]
 NOALLOC_MAX_RMAX = 256
 
@@ -97,6 +97,10 @@ def lib():
             "fskmc_stats": ([vp, C.POINTER(C.c_uint64)], C.c_int),
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
+            "fskmc_autotune": ([C.c_int32, C.POINTER(Lattice), C.c_int, C.POINTER(Rates), C.c_int,
+                                C.c_double, C.c_int, C.c_int, C.c_double, C.c_uint64, vp,
+                                C.POINTER(CellShape), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_double)], C.c_int),
             "fskmc_observables_noalloc": ([vp, C.c_int32, C.c_int32, C.c_int, vp,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
                                            C.POINTER(C.c_double), C.c_int32], C.c_int),
@@ -266,6 +270,24 @@ class Context:
 
     def sync(self):
         _check(lib().fskmc_sync(self.h), self.h)
+
+
+def autotune(batch, model, scheme, dt, clock="FP32", engine="PERSISTENT", coverage=0.5,
+             seed=0, stream=None):
+    """fskmc_autotune: fastest (q, warps per block, events/s) for a batch."""
+    n = len(batch)
+    lats = (Lattice * n)(*[Lattice(b["lx"], b["ly"], 0) for b in batch])
+    rts = (Rates * n)(*[_rates(b["rates"]) for b in batch])
+    cell = CellShape()
+    wpb = C.c_int32()
+    rate = C.c_double()
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    st = lib().fskmc_autotune(n, lats, m, rts, s, dt, CLOCKS[clock], ENGINES[engine], coverage,
+                              seed, _stream_ptr(stream), C.byref(cell), C.byref(wpb),
+                              C.byref(rate))
+    _check(st)
+    return (cell.qx, cell.qy), wpb.value, rate.value
 
 
 def observables_noalloc(lattice, lx: int, ly: int, model, rmax: int = 0, stream=None):

@@ -38,8 +38,8 @@ struct fskmc_ctx {
     uint64_t windows = 0;  // windows run
     fskmc_clock clock = FSKMC_CLOCK_FP64;
     fskmc_engine engine = FSKMC_ENGINE_PLAIN;
-    int wpb = 4;
-    uint32_t spin_limit = 1u << 24;
+    int wpb = 2;
+    uint32_t spin_limit = 1u << 20;
     cudaStream_t stream = nullptr;
     fskmc::PersistentState *pers = nullptr;
     std::string err;
@@ -673,6 +673,63 @@ fskmc_status fskmc_sync(fskmc_ctx *c)
 {
     if (!c) return FSKMC_EINVAL;
     CK(c, cudaStreamSynchronize(c->stream));
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_model model,
+                            const fskmc_rates *rates, fskmc_scheme scheme, double dt,
+                            fskmc_clock clock, fskmc_engine engine, double coverage, uint64_t seed,
+                            void *stream, fskmc_cell_shape *best_cell, int32_t *best_wpb,
+                            double *best_rate)
+{
+    if (!lattices || !rates || !best_cell || !best_wpb)
+        return fail(nullptr, FSKMC_EINVAL, "NULL argument");
+    if (!(dt > 0.0)) return fail(nullptr, FSKMC_EINVAL, "dt must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    double best = -1.0;
+    fskmc_cell_shape bc = {0, 0};
+    int bw = 0;
+    for (int q : {8, 16, 32}) {
+        fskmc_ctx *c = nullptr;
+        if (make_ctx(n, lattices, model, rates, fskmc_cell_shape{q, q}, stream, true, &c) != FSKMC_OK)
+            continue;  // this cell size does not fit every lattice
+        fskmc_status st = fskmc_set_clock(c, clock);
+        if (!st) st = fskmc_set_engine(c, engine);
+        if (!st) st = fskmc_init_random(c, seed, coverage);
+        for (int wpb : {2, 4, 8}) {
+            if (st || fskmc_set_warps_per_block(c, wpb) != FSKMC_OK) break;
+            // warm-up step, then a timed run of 4 steps from where it left off
+            st = fskmc_run(c, scheme, dt, dt, seed);
+            if (st) break;
+            uint64_t before[5], after[5];
+            if ((st = fskmc_stats(c, before)) != FSKMC_OK) break;
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+            st = fskmc_run(c, scheme, dt, 4.0 * dt, seed);
+            cudaEventRecord(b, s);
+            cudaEventSynchronize(b);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, a, b);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            if (st || (st = fskmc_stats(c, after)) != FSKMC_OK) break;
+            const double rate = ms > 0.0f ? (double)(after[0] - before[0]) / (ms * 1e-3) : 0.0;
+            if (rate > best) {
+                best = rate;
+                bc = fskmc_cell_shape{q, q};
+                bw = wpb;
+            }
+        }
+        fskmc_destroy(c);
+        if (st) return fail(nullptr, st, "autotune trial failed for q=%d", q);
+    }
+    if (best < 0.0) return fail(nullptr, FSKMC_EINVAL, "no cell size in {8,16,32} fits every lattice");
+    *best_cell = bc;
+    *best_wpb = bw;
+    if (best_rate) *best_rate = best;
+    g_create_error.clear();
     return FSKMC_OK;
 }
 

@@ -625,20 +625,18 @@ struct PParams {
     int32_t *abort_flag;
 };
 
-__device__ __forceinline__ int ld_acquire(const int32_t *p)
-{
-    cuda::atomic_ref<const int32_t, cuda::thread_scope_device> a(*p);
-    return a.load(cuda::memory_order_acquire);
-}
-
-// Lanes 0..nd-1 poll deps[lane] until epoch >= target. Returns false on
-// timeout or abort.
+// Lanes with has_dep poll ep[dep] until it reaches their target. Polls are
+// relaxed loads with exponential back-off (128 ns doubling to 4 us), so
+// waiting warps leave the issue slots to working ones; one acquire fence
+// after success orders the cell's later reads. Returns false on timeout
+// (after P.spin_limit polls) or when another warp raised the abort flag.
 __device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target,
-                            const PParams &P, int lane)  // target may differ per lane
+                            const PParams &P, int lane)
 {
     uint32_t spins = 0;
+    unsigned ns = 128;
     for (;;) {
-        bool ok = !has_dep || ld_acquire(ep + dep) >= target;
+        bool ok = !has_dep || *(volatile const int32_t *)(ep + dep) >= target;
         if (__all_sync(0xffffffffu, ok)) break;
         if (spins >= P.spin_limit) {
             if (lane == 0) {
@@ -648,11 +646,12 @@ __device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target
             return false;
         }
         ++spins;
-        if ((spins & 63u) == 0u) {
+        if ((spins & 15u) == 0u) {
             int ab = *(volatile int32_t *)P.abort_flag;
             if (__any_sync(0xffffffffu, ab != 0)) return false;
         }
-        __nanosleep(spins < 64 ? 20 : 200);
+        __nanosleep(ns);
+        if ((spins & 3u) == 0u && ns < 4096u) ns <<= 1;
     }
     __threadfence();
     __syncwarp();

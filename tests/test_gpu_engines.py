@@ -155,3 +155,15 @@ def test_bounded_wait_gives_up_cleanly():
         c.init_random(1, 0.5)
         c.run("LIE", 0.5, 2.0, 1)
         assert c.stats()["check_failures"] == 0
+
+
+def test_autotuner_picks_a_valid_shape():
+    reps = _batch()
+    q, wpb, rate = F.autotune(reps, "ADSDES", "LIE", 0.1, clock="FP32", engine="PERSISTENT")
+    assert q[0] == q[1] and q[0] in (8, 16) and wpb in (2, 4, 8) and rate > 0
+    with F.Context(model="ADSDES", q=q, batch=reps) as b:
+        b.set_warps_per_block(wpb)
+        b.set_engine("PERSISTENT")
+        b.init_random(1, 0.5)
+        b.run("LIE", 0.1, 1.0, 1)
+        assert b.stats()["check_failures"] == 0
