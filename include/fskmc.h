@@ -231,6 +231,18 @@ fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);
 fskmc_status fskmc_sync(fskmc_ctx *ctx);
 
 /*
+ * Self-test of the binary64 window clock's divide. The waiting time
+ * -log(u_t)/lambda of the binary64 contract (Eqs. totalrate/skeleton) is
+ * computed on the integer pipes (exact quotient and remainder of the
+ * significands, rounded to nearest even); this compares it with the
+ * hardware correctly rounded divide on the n pairs (a[i] >= 0, b[i] > 0,
+ * host arrays) and writes the number of disagreeing pairs to *mismatches
+ * (must be 0). Runs on the current device. EINVAL: NULL pointers, n < 0.
+ */
+fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
+                                   uint32_t *mismatches);
+
+/*
  * Autotuner for the batched workload: for every square cell size q in
  * {8, 16, 32} that all n lattices admit and warps per block in {2, 4, 8},
  * builds a scratch batch context (lattices[n], rates[n], model; Bernoulli

@@ -35,7 +35,7 @@ EXPORTS = [
     "fskmc_set_spin_limit", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
-    "fskmc_observables_noalloc", "fskmc_autotune",
+    "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide",
 ]
 NOALLOC_MAX_RMAX = 256
 
@@ -97,6 +97,7 @@ def lib():
             "fskmc_stats": ([vp, C.POINTER(C.c_uint64)], C.c_int),
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
+            "fskmc_selftest_divide": ([vp, vp, C.c_int32, C.POINTER(C.c_uint32)], C.c_int),
             "fskmc_autotune": ([C.c_int32, C.POINTER(Lattice), C.c_int, C.POINTER(Rates), C.c_int,
                                 C.c_double, C.c_int, C.c_int, C.c_double, C.c_uint64, vp,
                                 C.POINTER(CellShape), C.POINTER(C.c_int32),
@@ -270,6 +271,15 @@ class Context:
 
     def sync(self):
         _check(lib().fskmc_sync(self.h), self.h)
+
+
+def selftest_divide(a, b) -> int:
+    """fskmc_selftest_divide: mismatches of the kernel's divide vs the hardware's."""
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    bad = C.c_uint32()
+    _check(lib().fskmc_selftest_divide(a.ctypes.data, b.ctypes.data, len(a), C.byref(bad)))
+    return bad.value
 
 
 def autotune(batch, model, scheme, dt, clock="FP32", engine="PERSISTENT", coverage=0.5,

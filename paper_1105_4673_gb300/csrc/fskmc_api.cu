@@ -676,6 +676,29 @@ fskmc_status fskmc_sync(fskmc_ctx *c)
     return FSKMC_OK;
 }
 
+fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
+                                   uint32_t *mismatches)
+{
+    if (!a || !b || !mismatches || n < 0) return fail(nullptr, FSKMC_EINVAL, "bad self-test arguments");
+    double *da = nullptr, *db = nullptr;
+    unsigned int *dbad = nullptr;
+    cudaError_t e = cudaMalloc(&da, sizeof(double) * (size_t)n + 8);
+    if (e == cudaSuccess) e = cudaMalloc(&db, sizeof(double) * (size_t)n + 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dbad, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpy(da, a, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(db, b, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dbad, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = fskmc::launch_div_selftest(da, db, n, dbad, nullptr);
+    unsigned int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, dbad, sizeof bad, cudaMemcpyDeviceToHost);
+    cudaFree(da);
+    cudaFree(db);
+    cudaFree(dbad);
+    if (e != cudaSuccess) return fail(nullptr, FSKMC_ECUDA, "self-test: %s", cudaGetErrorString(e));
+    *mismatches = bad;
+    return FSKMC_OK;
+}
+
 fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_model model,
                             const fskmc_rates *rates, fskmc_scheme scheme, double dt,
                             fskmc_clock clock, fskmc_engine engine, double coverage, uint64_t seed,

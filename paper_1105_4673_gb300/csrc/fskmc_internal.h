@@ -85,6 +85,11 @@ cudaError_t launch_init_bump(uint8_t *lat, int lx, int ly, uint64_t seed, const 
 cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
                                unsigned long long *out, cudaStream_t s);
 
+// Self-test of the window kernel's integer-pipe division against the
+// hardware correctly rounded divide: counts disagreeing pairs into *bad.
+cudaError_t launch_div_selftest(const double *a, const double *b, int n, unsigned int *bad,
+                                cudaStream_t s);
+
 // Validation of a lattice: counts bytes >= nstates into *bad.
 cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned int *bad,
                             cudaStream_t s);

@@ -128,6 +128,57 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
 // Bit pattern of a non-negative double: orders like the value.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
+// x (0 < x < 2^63) as a binary32 with its significand truncated to 24 bits,
+// built on the integer pipes (the 64-bit conversion instruction runs on the
+// FP64 pipe).
+__device__ __forceinline__ float u64_to_float_rz(uint64_t x)
+{
+    const int lz = __clzll((long long)x);
+    const uint32_t m = (uint32_t)((x << lz) >> 40);
+    return __uint_as_float(((uint32_t)(190 - lz) << 23) | (m & 0x7FFFFFu));
+}
+
+}  // namespace
+
+// a / b rounded to nearest (ties to even) for a >= 0 and b > 0, computed on
+// the integer pipes: with 53-bit significands ma, mb the quotient
+// significand is Q = floor(ma 2^s / mb) in [2^52, 2^53) (s = 52 or 53) and
+// the exact remainder R = ma 2^s - Q mb decides the rounding (2R vs mb). On
+// GB300 the FP64 pipe is the window kernel's bottleneck; this keeps the
+// divide off it. Cases whose result would not be a normal number (or whose
+// divisor is subnormal) go to the hardware divide.
+__device__ double div_rn(double a, double b)
+{
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    if (A == 0ull) return 0.0;
+    const long long ea = (long long)(A >> 52), eb = (long long)(B >> 52);
+    if (ea == 0 || eb == 0 || ea == 2047 || eb == 2047) return __ddiv_rn(a, b);
+    const unsigned long long FRAC = (1ull << 52) - 1ull;
+    const unsigned long long ma = (A & FRAC) | (1ull << 52), mb = (B & FRAC) | (1ull << 52);
+    long long e = ea - eb + 1023;
+    unsigned __int128 N;
+    if (ma >= mb) {
+        N = (unsigned __int128)ma << 52;
+    } else {
+        N = (unsigned __int128)ma << 53;
+        e -= 1;
+    }
+    if (e < 1 || e > 2045) return __ddiv_rn(a, b);
+    unsigned long long Q = (unsigned long long)(N / mb);
+    const unsigned long long R = (unsigned long long)(N - (unsigned __int128)Q * mb);
+    if (2ull * R > mb || (2ull * R == mb && (Q & 1ull))) {
+        Q += 1ull;
+        if (Q == (1ull << 53)) {
+            Q >>= 1;
+            e += 1;
+        }
+    }
+    return __longlong_as_double((long long)(((unsigned long long)e << 52) | (Q & FRAC)));
+}
+
+namespace {
+
 struct Layout {
     int BW, BH, nsite, s, SW;
     int box_bytes, scls_bytes, sitemask_words, slotmask_words;
@@ -345,7 +396,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         if (F64) {
             const double l = __shfl_sync(0xffffffffu, rl, src_lane);
             const double uc = __shfl_sync(0xffffffffu, ruc, src_lane);
-            const double end = __dadd_rn(tau, __ddiv_rn(l, lamd));
+            const double end = __dadd_rn(tau, div_rn(l, lamd));
             const long long eb = dbits(end);
             if (llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
             if (eb >= hbits) break;
@@ -358,7 +409,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         } else {
             const float l = __shfl_sync(0xffffffffu, rlf, src_lane);
             const uint32_t w2 = __shfl_sync(0xffffffffu, rw2, src_lane);
-            const float lamf = __fmul_rn(__ull2float_rn(lami), qscale);
+            const float lamf = __fmul_rn(u64_to_float_rz(lami), qscale);
             const float end = __fadd_rn(tauf, __fdividef(l, lamf));
             if (end >= hf) break;
             tauf = end;
@@ -969,6 +1020,22 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     PCK(cudaStreamSynchronize(s));
     if (*st->h_abort) { *msg = "a bounded wait gave up"; return cudaErrorTimeout; }
     return cudaSuccess;
+}
+
+__global__ void div_selftest_kernel(const double *a, const double *b, int n, unsigned int *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double x = div_rn(a[i], b[i]), y = __ddiv_rn(a[i], b[i]);
+        if (__double_as_longlong(x) != __double_as_longlong(y)) atomicAdd(bad, 1u);
+    }
+}
+
+cudaError_t launch_div_selftest(const double *a, const double *b, int n, unsigned int *bad,
+                                cudaStream_t s)
+{
+    if (n > 0) div_selftest_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, b, n, bad);
+    return cudaGetLastError();
 }
 
 }  // namespace fskmc

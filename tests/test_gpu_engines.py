@@ -167,3 +167,28 @@ def test_autotuner_picks_a_valid_shape():
         b.init_random(1, 0.5)
         b.run("LIE", 0.1, 1.0, 1)
         assert b.stats()["check_failures"] == 0
+
+
+def test_integer_divide_matches_hardware():
+    """The binary64 waiting time divides on the integer pipes; it must agree
+    bit for bit with the hardware correctly rounded divide, including exact
+    quotients, zero numerators, and quotients outside the normal range
+    (handled by the fallback)."""
+    rng = np.random.default_rng(7)
+    n = 1 << 21
+    a = 40.0 * rng.random(n)
+    a[::5] *= 1e-10
+    a[::97] = 0.0
+    b = 1e-6 * np.exp(32.0 * rng.random(n))
+    b[::101] = 1.0
+    b[::103] = 3.0
+    a[::103] = 3.0 * np.arange(len(a[::103]))
+    # extreme ratios: results beyond the normal range use the fallback
+    a[1:200] = 1e300
+    b[1:200] = 1e-300
+    a[200:400] = 1e-300
+    b[200:400] = 1e300
+    # significands straddling: a's below and above b's
+    a[400:600] = np.nextafter(b[400:600], 0)
+    a[600:800] = np.nextafter(b[600:800], np.inf)
+    assert F.selftest_divide(a, b) == 0
