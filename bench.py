@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--workload", default="ising1024")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--engine", default="plain", choices=["plain", "persistent"])
+    p.add_argument("--clock", default="fp64", choices=["fp64", "fp32"])
     return p.parse_args()
 
 
@@ -117,6 +119,22 @@ FP64_OPS_PER_EVENT = 10 + 4
 # Peak: the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp instructions,
 # 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
 FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
+# The binary32 clock's per-event algorithmic work is the same contract with
+# integer class sums; its peak is the INT32/FP32 warp-instruction issue rate,
+# 152 SMs x 4 schedulers x 2.07 GHz.
+ISSUE_PEAK_G = 152 * 4 * 2.07
+
+# DRAM traffic per launch of fs_window_kernel<ISING,double> on this workload
+# from one ncu capture (profiles/fs_window_kernel_ising1024.md), valid only
+# for the kernel source it was taken on.
+PROFILED_TRAFFIC = {"src_sha256": "491f2df9b98e269b240e78d3bb53ff9711d1a50547052bc0860fc43176abb224",
+                    "bytes_per_launch": 1087744}
+
+
+def window_src_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1105_4673_gb300", "csrc", "fskmc_window.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
 
 
 def cpu_baseline(w, seconds):
@@ -130,10 +148,10 @@ def cpu_baseline(w, seconds):
                        oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
     t0 = time.process_time()
     steps = 0
-    while time.process_time() - t0 < seconds:
+    while steps == 0 or time.process_time() - t0 < seconds:
         run.run(w["scheme"], w["dt"], w["dt"], w["seed"])
         steps += 1
-    dt = time.process_time() - t0
+    dt = max(time.process_time() - t0, 1e-9)
     return {"value": run.events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
             "sample": f"256x256 lattice, same model/rates/cells/schedule, {steps} Lie steps "
                       f"of dt={w['dt']} ({run.events} events, {dt:.1f} s CPU, single thread)"}
@@ -191,20 +209,32 @@ def main():
     lx, ly = w["lx"], w["ly"]
     seed = w["seed"] + 7919 * rank
     ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream)
+    ctx.set_engine(args.engine.upper())
+    ctx.set_clock(args.clock.upper())
     ctx.init_random(seed, w.get("coverage", 0.5))
     col, hh = schedule(w, STEP_T)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(kernel_events=None):
-        for c, h in zip(col, hh):
+        # plain engine: one window-kernel launch per window, each bracketed by
+        # events on the context's stream; persistent: one launch per run
+        if args.engine == "plain":
+            for c, h in zip(col, hh):
+                if kernel_events is not None:
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ctx.window(int(c), float(h), seed)
+                    b.record(stream)
+                    kernel_events.append((a, b))
+                else:
+                    ctx.window(int(c), float(h), seed)
+        else:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.run(w["scheme"], w["dt"], STEP_T, seed)
+            b.record(stream)
             if kernel_events is not None:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ctx.window(int(c), float(h), seed)
-                b.record(stream)
                 kernel_events.append((a, b))
-            else:
-                ctx.window(int(c), float(h), seed)
         return ctx.observables(0, RMAX)
 
     for _ in range(args.warmup):
@@ -261,25 +291,34 @@ def main():
     k_events_per_launch = events / max(len(kernel_ms), 1)
     k_avg_s = float(np.mean(kernel_ms)) / 1000.0
     achieved = k_events_per_launch * FP64_OPS_PER_EVENT / k_avg_s / 1e9
+    fp64 = args.clock == "fp64"
+    peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
+    kname = ("fs_window_kernel" if args.engine == "plain" else "fs_persistent_kernel") + \
+        ("<ISING,double>" if fp64 else "<ISING,float>")
+    traffic = None
+    if (args.engine == "plain" and fp64 and PROFILED_TRAFFIC["src_sha256"] == window_src_sha()):
+        traffic = PROFILED_TRAFFIC["bytes_per_launch"]
     cb = cpu_baseline(w, args.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32+u64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {lx}x{ly} {w['model']} betaJ="
                                f"{w['rates'].get('betaJ')} q={w['q'][0]} {w['scheme']} dt={w['dt']}",
                    "step": f"{STEP_T:g} time units ({len(col)} windows) + observables",
-                   "clock": "fp64", "engine": "plain", "l2": "flushed between timed steps"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_WARP_OPS_PEAK_G,
-                     "unit": "G fp64 warp-ops/s", "frac": achieved / FP64_WARP_OPS_PEAK_G,
-                     "traffic": None,
-                     "kernel": "fs_window_kernel<ISING,double>",
+                   "clock": args.clock, "engine": args.engine,
+                   "l2": "flushed between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "G fp64 warp-ops/s" if fp64 else "G warp-ops/s", "frac": achieved / peak,
+                     "traffic": traffic,
+                     "kernel": kname,
                      "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
                      "events_per_launch": k_events_per_launch,
-                     "fp64_ops_per_event": FP64_OPS_PER_EVENT,
-                     "peak_note": "derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA; "
-                                  "HBM is not the bound (2.27 B/site/window)"},
+                     "algorithmic_ops_per_event": FP64_OPS_PER_EVENT,
+                     "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
+                                   if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz") +
+                                  "; HBM is not the bound (2.27 B/site/window)"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
                 "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
