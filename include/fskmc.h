@@ -195,6 +195,19 @@ fskmc_status fskmc_get_state(fskmc_ctx *ctx, int32_t replica, uint8_t *dst,
 fskmc_status fskmc_run(fskmc_ctx *ctx, fskmc_scheme scheme, double dt, double T,
                        uint64_t seed);
 
+/*
+ * The windows a run of time T would execute (the processor communication
+ * schedule of Section 3: Eq. lie, Eq. strang, Eq. SLPCS), starting at global
+ * window index w0 for the given replica id: colour[i] (0 = E, 1 = O) and
+ * length h[i]. With colour == h == NULL only *nwindows is set. RANDOM draws
+ * each window's colour, RANDOM_ORDER each step's order, from bit 0 of word 0
+ * of Philox(seed, (0, w, 0, replica | 3<<24)). EINVAL: as fskmc_run, or
+ * arrays shorter than *nwindows.
+ */
+fskmc_status fskmc_schedule(fskmc_scheme scheme, double dt, double T, uint64_t seed,
+                            uint32_t replica, uint64_t w0, int32_t *colour, double *h,
+                            int64_t cap, int64_t *nwindows);
+
 /* One window of colour (0 = E, 1 = O) and length h at the current window
    index (then incremented), for every replica. EINVAL: h <= 0, colour not 0/1. */
 fskmc_status fskmc_window(fskmc_ctx *ctx, int32_t colour, double h, uint64_t seed);

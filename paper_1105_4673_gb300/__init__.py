@@ -35,7 +35,7 @@ EXPORTS = [
     "fskmc_set_spin_limit", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
-    "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide",
+    "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_schedule",
 ]
 NOALLOC_MAX_RMAX = 256
 
@@ -98,6 +98,8 @@ def lib():
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
             "fskmc_selftest_divide": ([vp, vp, C.c_int32, C.POINTER(C.c_uint32)], C.c_int),
+            "fskmc_schedule": ([C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32, C.c_uint64,
+                                vp, vp, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
             "fskmc_autotune": ([C.c_int32, C.POINTER(Lattice), C.c_int, C.POINTER(Rates), C.c_int,
                                 C.c_double, C.c_int, C.c_int, C.c_double, C.c_uint64, vp,
                                 C.POINTER(CellShape), C.POINTER(C.c_int32),
@@ -271,6 +273,18 @@ class Context:
 
     def sync(self):
         _check(lib().fskmc_sync(self.h), self.h)
+
+
+def schedule(scheme, dt: float, T: float, seed: int = 0, replica: int = 0, w0: int = 0):
+    """fskmc_schedule: (colours, lengths) of the windows of a run."""
+    s = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    n = C.c_int64()
+    _check(lib().fskmc_schedule(s, dt, T, seed, replica, w0, None, None, 0, C.byref(n)))
+    col = np.zeros(max(n.value, 1), np.int32)
+    h = np.zeros(max(n.value, 1), np.float64)
+    _check(lib().fskmc_schedule(s, dt, T, seed, replica, w0, col.ctypes.data, h.ctypes.data,
+                                n.value, C.byref(n)))
+    return col[:n.value], h[:n.value]
 
 
 def selftest_divide(a, b) -> int:

@@ -676,6 +676,29 @@ fskmc_status fskmc_sync(fskmc_ctx *c)
     return FSKMC_OK;
 }
 
+fskmc_status fskmc_schedule(fskmc_scheme scheme, double dt, double T, uint64_t seed,
+                            uint32_t replica, uint64_t w0, int32_t *colour, double *h,
+                            int64_t cap, int64_t *nwindows)
+{
+    if (!nwindows) return fail(nullptr, FSKMC_EINVAL, "NULL nwindows");
+    if ((int)scheme < 0 || (int)scheme > 3) return fail(nullptr, FSKMC_EINVAL, "unknown scheme %d", (int)scheme);
+    if (replica >= (1u << 24)) return fail(nullptr, FSKMC_EINVAL, "replica id must be < 2^24");
+    const int64_t n = nsteps(dt, T);
+    if (n < 0) return fail(nullptr, FSKMC_EINVAL, "dt must be > 0, T >= 0 and T/dt an integer");
+    std::vector<Win> sched;
+    build_schedule(scheme, n, dt, seed, replica, w0, sched);
+    *nwindows = (int64_t)sched.size();
+    if (!colour && !h) return FSKMC_OK;
+    if (!colour || !h || cap < (int64_t)sched.size())
+        return fail(nullptr, FSKMC_EINVAL, "output arrays missing or too small (%lld windows)",
+                    (long long)sched.size());
+    for (size_t i = 0; i < sched.size(); ++i) {
+        colour[i] = sched[i].colour;
+        h[i] = sched[i].h;
+    }
+    return FSKMC_OK;
+}
+
 fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
                                    uint32_t *mismatches)
 {

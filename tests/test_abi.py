@@ -67,3 +67,17 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.fskmc_sync(None) == F.EINVAL
     assert lib.fskmc_stats(None, None) == F.EINVAL
     lib.fskmc_destroy(None)
+
+
+@pytest.mark.parametrize("scheme", ["LIE", "STRANG", "RANDOM", "RANDOM_ORDER"])
+@pytest.mark.parametrize("replica,w0", [(0, 0), (5, 1234), (77, 2**31)])
+def test_schedule_matches_oracle(lib, scheme, replica, w0):
+    """Row a2 (schedules, Section 3): the library's window list equals the
+    oracle's, window for window (host code, no GPU needed)."""
+    import numpy as np
+    import oracle
+    col, h = F.schedule(scheme, 0.05, 3.0, seed=0xABCDEF, replica=replica, w0=w0)
+    ocol, oh = oracle.schedule(scheme, 0.05, 3.0, seed=0xABCDEF, replica=replica, w0=w0)
+    assert np.array_equal(col, ocol) and np.array_equal(h, oh)
+    with pytest.raises(F.FskmcError):
+        F.schedule(scheme, 0.07, 1.0)
