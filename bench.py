@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 from workloads import WORKLOADS  # noqa: E402
 
 METRIC = "KMC events/sec on 1 GB300 (batched FP32-clock vs plain FP64) at stated Δt-error"
-STEP_T = 10.0
+STEP_WINDOWS_DT = 10  # one bench step advances the lattice by 10 dt of physical time
 RMAX = 32
 L2_FLUSH_BYTES = 256 << 20
 
@@ -111,11 +111,12 @@ class ClockSampler:
 
 
 # Roofline of the binary64 window kernel: it is bound by the FP64 pipe
-# (ncu: ~82% of its peak). Algorithmic binary64 operations per event of the
-# contract, each a warp-uniform instruction of the cell's warp: the ordered
-# fused multiply-add chain over the 10 Ising classes, the divide, the
-# threshold multiply, the clock add and the logarithm.
-FP64_OPS_PER_EVENT = 10 + 4
+# (ncu: ~62% of its peak, the rest of the time the dependent chain).
+# Algorithmic binary64 operations per event of the contract, each a
+# warp-uniform instruction of the cell's warp: the ordered fused
+# multiply-add chain over the model's K classes, the divide, the threshold
+# multiply, the clock add and the logarithm.
+NCLASSES = {"ADSDES": 10, "ISING": 10, "DIFFUSION": 15, "ZGB": 4}
 # Peak: the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp instructions,
 # 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
 FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
@@ -207,18 +208,19 @@ def main():
     stream = torch.cuda.current_stream(dev)
     w = WORKLOADS[args.workload]
     lx, ly = w["lx"], w["ly"]
-    seed = w["seed"] + 7919 * rank
+    seed = rank_seed(w["seed"], rank)
     ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream)
     ctx.set_engine(args.engine.upper())
     ctx.set_clock(args.clock.upper())
     ctx.init_random(seed, w.get("coverage", 0.5))
-    col, hh = schedule(w, STEP_T)
+    step_t = STEP_WINDOWS_DT * w["dt"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(kernel_events=None):
         # plain engine: one window-kernel launch per window, each bracketed by
         # events on the context's stream; persistent: one launch per run
         if args.engine == "plain":
+            col, hh = F.schedule(w["scheme"], w["dt"], step_t, seed, 0, ctx.window_index)
             for c, h in zip(col, hh):
                 if kernel_events is not None:
                     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -231,7 +233,7 @@ def main():
         else:
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ctx.run(w["scheme"], w["dt"], STEP_T, seed)
+            ctx.run(w["scheme"], w["dt"], step_t, seed)
             b.record(stream)
             if kernel_events is not None:
                 kernel_events.append((a, b))
@@ -273,7 +275,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.set_state(hnp)
-        ctx.run(w["scheme"], w["dt"], STEP_T, seed)
+        ctx.run(w["scheme"], w["dt"], step_t, seed)
         ctx.observables(0, RMAX)
         ctx.get_state(0, hnp)
     torch.cuda.synchronize()
@@ -290,13 +292,15 @@ def main():
     cs = clk.summary()
     k_events_per_launch = events / max(len(kernel_ms), 1)
     k_avg_s = float(np.mean(kernel_ms)) / 1000.0
-    achieved = k_events_per_launch * FP64_OPS_PER_EVENT / k_avg_s / 1e9
+    ops_per_event = NCLASSES[w["model"]] + 4
+    achieved = k_events_per_launch * ops_per_event / k_avg_s / 1e9
     fp64 = args.clock == "fp64"
     peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
     kname = ("fs_window_kernel" if args.engine == "plain" else "fs_persistent_kernel") + \
-        ("<ISING,double>" if fp64 else "<ISING,float>")
+        (f"<{w['model']},double>" if fp64 else f"<{w['model']},float>")
     traffic = None
-    if (args.engine == "plain" and fp64 and PROFILED_TRAFFIC["src_sha256"] == window_src_sha()):
+    if (args.engine == "plain" and fp64 and args.workload == "ising1024"
+            and PROFILED_TRAFFIC["src_sha256"] == window_src_sha()):
         traffic = PROFILED_TRAFFIC["bytes_per_launch"]
     cb = cpu_baseline(w, args.cpu_seconds)
     out = {
@@ -306,7 +310,8 @@ def main():
         "dtype": "f64" if fp64 else "f32+u64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {lx}x{ly} {w['model']} betaJ="
                                f"{w['rates'].get('betaJ')} q={w['q'][0]} {w['scheme']} dt={w['dt']}",
-                   "step": f"{STEP_T:g} time units ({len(col)} windows) + observables",
+                   "step": f"{step_t:g} time units ({kernel_windows_per_step(F, w, step_t)} windows) "
+                           "+ observables",
                    "clock": args.clock, "engine": args.engine,
                    "l2": "flushed between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
@@ -315,7 +320,7 @@ def main():
                      "kernel": kname,
                      "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
                      "events_per_launch": k_events_per_launch,
-                     "algorithmic_ops_per_event": FP64_OPS_PER_EVENT,
+                     "algorithmic_ops_per_event": ops_per_event,
                      "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
                                    if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz") +
                                   "; HBM is not the bound (2.27 B/site/window)"},
@@ -345,13 +350,14 @@ def measure_variants(F, w, stream, seed, steps):
         c.set_engine(engine)
         c.set_clock(clock)
         c.init_random(seed, w.get("coverage", 0.5))
-        c.run(w["scheme"], w["dt"], STEP_T, seed)
+        step_t = STEP_WINDOWS_DT * w["dt"]
+        c.run(w["scheme"], w["dt"], step_t, seed)
         torch.cuda.synchronize()
         e0 = c.stats()["events"]
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(steps):
-            c.run(w["scheme"], w["dt"], STEP_T, seed)
+            c.run(w["scheme"], w["dt"], step_t, seed)
         b.record(stream)
         torch.cuda.synchronize()
         ev = c.stats()["events"] - e0
@@ -429,15 +435,8 @@ def clock_error(F, stream, w, n=64, L=128, T=10.0):
     return out
 
 
-def schedule(w, T):
-    # the window sequence of one step (fixed schedules only)
-    if w["scheme"] == "LIE":
-        n = int(round(T / w["dt"]))
-        return [0, 1] * n, [w["dt"]] * (2 * n)
-    if w["scheme"] == "STRANG":
-        n = int(round(T / w["dt"]))
-        return [0, 1, 0] * n, [w["dt"] / 2, w["dt"], w["dt"] / 2] * n
-    raise ValueError("bench steps use a deterministic schedule")
+def kernel_windows_per_step(F, w, step_t):
+    return len(F.schedule(w["scheme"], w["dt"], step_t)[0])
 
 
 def barrier(world):
@@ -446,24 +445,32 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    """Slowest rank's time (the job's time)."""
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX) if world > 1 else x
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
+    """Whole-job count (events of all ranks)."""
     import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM) if world > 1 else x
+
+
+def rank_seed(base, rank):
+    """Each rank simulates its own independent lattice (weak scaling)."""
+    return base + 7919 * rank
 
 
 if __name__ == "__main__":
