@@ -209,7 +209,8 @@ def main():
     w = WORKLOADS[args.workload]
     lx, ly = w["lx"], w["ly"]
     seed = rank_seed(w["seed"], rank)
-    ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream)
+    ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream,
+                    bitpacked=w.get("bitpacked", False))
     ctx.set_engine(args.engine.upper())
     ctx.set_clock(args.clock.upper())
     ctx.init_random(seed, w.get("coverage", 0.5))
@@ -313,6 +314,7 @@ def main():
                    "step": f"{step_t:g} time units ({kernel_windows_per_step(F, w, step_t)} windows) "
                            "+ observables",
                    "clock": args.clock, "engine": args.engine,
+                   "storage": "1 bit/site" if w.get("bitpacked") else "1 byte/site",
                    "l2": "flushed between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "G fp64 warp-ops/s" if fp64 else "G warp-ops/s", "frac": achieved / peak,
@@ -346,7 +348,8 @@ def measure_variants(F, w, stream, seed, steps):
     res["ensemble512_persistent_fp64"] = ensemble_rate(F, stream, "FP64")
     res["fp32_vs_fp64"] = clock_error(F, stream, w)
     for engine, clock in (("PERSISTENT", "FP64"), ("PERSISTENT", "FP32"), ("PLAIN", "FP32")):
-        c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream)
+        c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream,
+                      bitpacked=w.get("bitpacked", False))
         c.set_engine(engine)
         c.set_clock(clock)
         c.init_random(seed, w.get("coverage", 0.5))

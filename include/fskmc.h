@@ -90,7 +90,9 @@ typedef enum { FSKMC_ENGINE_PLAIN = 0, FSKMC_ENGINE_PERSISTENT = 1 } fskmc_engin
 
 typedef struct {
     int32_t lx, ly;    /* lattice sides; lx % (2 qx) == 0 and ly % (2 qy) == 0 */
-    int32_t bitpacked; /* reserved, must be 0 */
+    int32_t bitpacked; /* 1: keep the lattice in device memory at 1 bit per site (32 sites of a
+                          row per 32-bit word); spin-flip models only, lx % 32 == 0. The ABI
+                          still exchanges one byte per site. Results are identical. */
 } fskmc_lattice;
 
 typedef struct {

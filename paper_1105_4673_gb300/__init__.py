@@ -153,18 +153,18 @@ class Context:
     """One library context (a single lattice or a batch of replicas)."""
 
     def __init__(self, lx=None, ly=None, model="ADSDES", rates=None, q=(8, 8), stream=None,
-                 batch=None):
+                 batch=None, bitpacked=False):
         L = lib()
         h = C.c_void_p()
         m = MODELS[model] if isinstance(model, str) else int(model)
         shape = CellShape(*(q if q is not None else (0, 0)))
         if batch is None:
             self.sizes = [(lx, ly)]
-            st = L.fskmc_create(C.byref(Lattice(lx, ly, 0)), m, C.byref(_rates(rates or {})),
+            st = L.fskmc_create(C.byref(Lattice(lx, ly, int(bitpacked))), m, C.byref(_rates(rates or {})),
                                 shape, _stream_ptr(stream), C.byref(h))
         else:
             n = len(batch)
-            lats = (Lattice * n)(*[Lattice(b["lx"], b["ly"], 0) for b in batch])
+            lats = (Lattice * n)(*[Lattice(b["lx"], b["ly"], int(bitpacked)) for b in batch])
             rts = (Rates * n)(*[_rates(b["rates"]) for b in batch])
             self.sizes = [(b["lx"], b["ly"]) for b in batch]
             st = L.fskmc_batch_create(n, lats, m, rts, shape, _stream_ptr(stream), C.byref(h))

@@ -27,6 +27,8 @@ struct fskmc_ctx {
     Replica *d_reps = nullptr;
     uint8_t *d_lat[2] = {nullptr, nullptr};  // [1] only for the ping-pong model
     int cur = 0;                             // which buffer holds the state
+    bool packed = false;                     // 1 bit per site in device memory
+    uint8_t *d_stage = nullptr;              // byte-per-site staging (packed contexts)
     int64_t total_sites = 0;
     int32_t total_cells = 0;
     int32_t *d_workload = nullptr;
@@ -133,7 +135,11 @@ fskmc_status check_rates(int model, const fskmc_rates &q)
 
 fskmc_status check_geometry(int model, const fskmc_lattice &L, int qx, int qy)
 {
-    if (L.bitpacked != 0) return fail(nullptr, FSKMC_EINVAL, "bitpacked lattices are not supported");
+    if (L.bitpacked != 0 && L.bitpacked != 1) return fail(nullptr, FSKMC_EINVAL, "bitpacked must be 0 or 1");
+    if (L.bitpacked && model != fskmc::ADSDES && model != fskmc::ISING)
+        return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices are for the spin-flip models");
+    if (L.bitpacked && L.lx % 32)
+        return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices need lx to be a multiple of 32");
     if (qx < 1 || qy < 1 || qx > fskmc::MAX_Q || qy > fskmc::MAX_Q)
         return fail(nullptr, FSKMC_EINVAL, "cell shape %dx%d out of range 1..32", qx, qy);
     if (L.lx < 2 * qx || L.ly < 2 * qy || L.lx % (2 * qx) || L.ly % (2 * qy))
@@ -250,6 +256,8 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
         qx = qy = best;
     }
     for (int r = 0; r < n; ++r) {
+        if (lats[r].bitpacked != lats[0].bitpacked)
+            return fail(nullptr, FSKMC_EINVAL, "all replicas must share the bit-packed setting");
         fskmc_status st = check_geometry(model, lats[r], qx, qy);
         if (st) return st;
         st = check_rates(model, rates[r]);
@@ -262,6 +270,7 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
     c->qx = qx;
     c->qy = qy;
     c->batch = batch;
+    c->packed = lats[0].bitpacked != 0;
     c->stream = (cudaStream_t)stream;
     c->reps.resize(n);
     int64_t off = 0;
@@ -278,9 +287,12 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
         R.rep = (uint32_t)r;
         c->nclass = class_rates(model, rates[r], R.r);
         set_fixed_point(R, c->nclass, qx * qy * ((int)model >= fskmc::DIFFUSION ? 9 : 1));
-        off += ((int64_t)R.lx * R.ly + 255) & ~(int64_t)255;
+        const int64_t bytes = c->packed ? (int64_t)(R.lx / 32) * R.ly * 4 : (int64_t)R.lx * R.ly;
+        off += (bytes + 255) & ~(int64_t)255;
         coff += R.ncx * R.ncy;
     }
+    int64_t max_sites = 0;
+    for (const Replica &R : c->reps) max_sites = std::max(max_sites, (int64_t)R.lx * R.ly);
     c->total_sites = off;
     c->total_cells = coff;
     cudaError_t e;
@@ -290,6 +302,7 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
     if (e == cudaSuccess) e = cudaMalloc(&c->d_workload, sizeof(int32_t) * (size_t)coff);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch_u32, sizeof(unsigned int) * 4);
+    if (e == cudaSuccess && c->packed) e = cudaMalloc(&c->d_stage, (size_t)max_sites);
     if (e != cudaSuccess) {
         fskmc_destroy(c);
         return fail(nullptr, e == cudaErrorMemoryAllocation ? FSKMC_ENOMEM : FSKMC_ECUDA,
@@ -339,6 +352,7 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         a.dst = pingpong ? c->d_lat[1 - c->cur] : c->d_lat[c->cur];
         a.workload = c->d_workload;
         a.counters = c->d_counters;
+        a.packed = c->packed ? 1 : 0;
         const Replica &R = c->reps[r];
         int nactive = R.ncx * R.ncy / 2;
         CK(c, fskmc::launch_window(c->model, fp32, a, nactive, c->wpb, c->stream));
@@ -379,6 +393,7 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         pr.seed = seed;
         pr.wpb = std::min(c->wpb, 8);  // the persistent kernel is built for <= 256 threads
         pr.spin_limit = c->spin_limit;
+        pr.packed = c->packed;
         std::string msg;
         cudaError_t e = fskmc::persistent_run(&c->pers, pr, c->stream, &msg);
         if (e == cudaErrorTimeout) {
@@ -395,6 +410,22 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         }
     }
     return FSKMC_OK;
+}
+
+// Byte-per-site view of a replica's lattice for the init/copy kernels: the
+// replica's own storage, or the staging buffer of a packed context.
+uint8_t *byte_view(fskmc_ctx *c, int r)
+{
+    return c->packed ? c->d_stage : c->d_lat[c->cur] + c->reps[r].lat_off;
+}
+
+// Packed contexts: pack the staging buffer into replica r's words.
+cudaError_t commit_view(fskmc_ctx *c, int r)
+{
+    if (!c->packed) return cudaSuccess;
+    const Replica &R = c->reps[r];
+    return fskmc::launch_pack(c->d_stage, reinterpret_cast<uint32_t *>(c->d_lat[c->cur] + R.lat_off),
+                              R.lx, R.ly, c->stream);
 }
 
 }  // namespace
@@ -426,6 +457,7 @@ void fskmc_destroy(fskmc_ctx *c)
     cudaFree(c->d_workload);
     cudaFree(c->d_counters);
     cudaFree(c->d_scratch_u32);
+    cudaFree(c->d_stage);
     cudaFree(c->d_obs);
     delete c;
 }
@@ -496,8 +528,9 @@ fskmc_status fskmc_init_random(fskmc_ctx *c, uint64_t seed, double coverage)
     if (!(coverage >= 0.0 && coverage <= 1.0)) return fail(c, FSKMC_EINVAL, "coverage must be in [0,1]");
     for (int r = 0; r < c->nrep; ++r) {
         const Replica &R = c->reps[r];
-        CK(c, fskmc::launch_init_bernoulli(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, seed, coverage,
-                                           R.rep, c->stream));
+        CK(c, fskmc::launch_init_bernoulli(byte_view(c, r), R.lx, R.ly, seed, coverage, R.rep,
+                                           c->stream));
+        CK(c, commit_view(c, r));
     }
     return FSKMC_OK;
 }
@@ -527,8 +560,9 @@ fskmc_status fskmc_init_bump(fskmc_ctx *c, uint64_t seed, double amp, double wid
         double *dg = nullptr;
         CK(c, cudaMallocAsync(&dg, sizeof(double) * g.size(), c->stream));
         CK(c, cudaMemcpyAsync(dg, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice, c->stream));
-        CK(c, fskmc::launch_init_bump(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, seed, dg, dg + R.lx,
-                                      amp, species, R.rep, c->stream));
+        CK(c, fskmc::launch_init_bump(byte_view(c, r), R.lx, R.ly, seed, dg, dg + R.lx, amp, species,
+                                      R.rep, c->stream));
+        CK(c, commit_view(c, r));
         CK(c, cudaFreeAsync(dg, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
@@ -541,7 +575,7 @@ fskmc_status fskmc_set_state(fskmc_ctx *c, int32_t replica, const uint8_t *src, 
     if (replica < 0 || replica >= c->nrep || !src) return fail(c, FSKMC_EINVAL, "bad replica or NULL src");
     const Replica &R = c->reps[replica];
     size_t n = (size_t)R.lx * R.ly;
-    uint8_t *dst = c->d_lat[c->cur] + R.lat_off;
+    uint8_t *dst = byte_view(c, replica);
     CK(c, cudaMemcpyAsync(dst, src, n, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           c->stream));
     CK(c, cudaMemsetAsync(c->d_scratch_u32, 0, sizeof(unsigned int), c->stream));
@@ -551,8 +585,10 @@ fskmc_status fskmc_set_state(fskmc_ctx *c, int32_t replica, const uint8_t *src, 
     CK(c, cudaStreamSynchronize(c->stream));
     if (bad) {
         CK(c, cudaMemsetAsync(dst, 0, n, c->stream));
+        CK(c, commit_view(c, replica));
         return fail(c, FSKMC_EINVAL, "%u sites hold a value that is not a state of the model", bad);
     }
+    CK(c, commit_view(c, replica));
     return FSKMC_OK;
 }
 
@@ -562,7 +598,10 @@ fskmc_status fskmc_get_state(fskmc_ctx *c, int32_t replica, uint8_t *dst, int32_
     if (replica < 0 || replica >= c->nrep || !dst) return fail(c, FSKMC_EINVAL, "bad replica or NULL dst");
     const Replica &R = c->reps[replica];
     size_t n = (size_t)R.lx * R.ly;
-    CK(c, cudaMemcpyAsync(dst, c->d_lat[c->cur] + R.lat_off, n,
+    if (c->packed)
+        CK(c, fskmc::launch_unpack(reinterpret_cast<const uint32_t *>(c->d_lat[c->cur] + R.lat_off),
+                                   c->d_stage, R.lx, R.ly, c->stream));
+    CK(c, cudaMemcpyAsync(dst, c->packed ? c->d_stage : c->d_lat[c->cur] + R.lat_off, n,
                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!is_device) CK(c, cudaStreamSynchronize(c->stream));
     return FSKMC_OK;
@@ -629,7 +668,8 @@ fskmc_status fskmc_observables(fskmc_ctx *c, int32_t replica, double *coverage, 
         c->obs_cap = need;
     }
     CK(c, cudaMemsetAsync(c->d_obs, 0, sizeof(unsigned long long) * need, c->stream));
-    CK(c, fskmc::launch_observables(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, rmax, c->d_obs, c->stream));
+    CK(c, fskmc::launch_observables(c->d_lat[c->cur] + R.lat_off, R.lx, R.ly, rmax, c->d_obs,
+                                    c->stream, c->packed));
     std::vector<unsigned long long> h(need);
     CK(c, cudaMemcpyAsync(h.data(), c->d_obs, sizeof(unsigned long long) * need, cudaMemcpyDeviceToHost,
                           c->stream));

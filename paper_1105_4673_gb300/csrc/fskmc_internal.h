@@ -16,6 +16,7 @@ struct Replica {
     int32_t lx, ly;      // lattice sides
     int32_t ncx, ncy;    // cells along x and y
     int64_t lat_off;     // byte offset of the replica's lattice in the lattice buffer
+                         // (one byte per site, or 32 sites per 32-bit word when packed)
     int32_t cell_off;    // index of the replica's cell 0 in per-cell arrays
     uint32_t rep;        // replica word of the random counters
     double r[MAX_CLASSES];       // class rates, binary64
@@ -64,6 +65,7 @@ struct WindowArgs {
     uint8_t *dst;              // result (== src when updated in place)
     int32_t *workload;         // events per cell in its latest window
     unsigned long long *counters;  // [0] events, [1] ambiguous cell-windows, [2] timeouts
+    int32_t packed;            // lattice stored 1 bit per site (spin-flip models)
 };
 
 // Shared-memory bytes one warp of the window kernel needs.
@@ -83,7 +85,12 @@ cudaError_t launch_init_bump(uint8_t *lat, int lx, int ly, uint64_t seed, const 
 // Integer observables: out[0..2] state counts, out[3] occupied NN pairs,
 // out[4 .. 4+rmax) G_x sums, out[4+rmax .. 4+2 rmax) G_y sums.
 cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
-                               unsigned long long *out, cudaStream_t s);
+                               unsigned long long *out, cudaStream_t s, bool packed = false);
+
+// Bit-packed storage: 32 consecutive sites of a row per 32-bit word, site x
+// in bit x % 32 of word y * lx/32 + x/32 (lx a multiple of 32).
+cudaError_t launch_pack(const uint8_t *bytes, uint32_t *words, int lx, int ly, cudaStream_t s);
+cudaError_t launch_unpack(const uint32_t *words, uint8_t *bytes, int lx, int ly, cudaStream_t s);
 
 // Self-test of the window kernel's integer-pipe division against the
 // hardware correctly rounded divide: counts disagreeing pairs into *bad.

@@ -46,8 +46,39 @@ __global__ void validate_kernel(const uint8_t *lat, int64_t n, int nstates, unsi
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
 
+__global__ void pack_kernel(const uint8_t *bytes, uint32_t *words, int64_t nwords)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t *b = bytes + 32 * i;
+        uint32_t w = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) w |= (uint32_t)(b[k] & 1u) << k;
+        words[i] = w;
+    }
+}
+
+__global__ void unpack_kernel(const uint32_t *words, uint8_t *bytes, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bytes[i] = (uint8_t)((words[i >> 5] >> (i & 31)) & 1u);
+}
+
+// Site (x, y) of a row-major lattice, one byte per site or bit-packed.
+template <bool PACKED>
+__device__ __forceinline__ int site_at(const uint8_t *lat, int lx, int y, int x)
+{
+    if (PACKED) {
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(lat);
+        return (int)((w[(int64_t)y * (lx >> 5) + (x >> 5)] >> (x & 31)) & 1u);
+    }
+    return lat[(int64_t)y * lx + x];
+}
+
 // One block per row (grid-stride over rows). Accumulators in shared memory
 // as 32-bit per block, flushed with 64-bit atomics.
+template <bool PACKED>
 __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
                                    unsigned long long *out)
 {
@@ -57,17 +88,17 @@ __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int y = blockIdx.x; y < ly; y += gridDim.x) {
-        const uint8_t *row = lat + (int64_t)y * lx;
-        const uint8_t *down = lat + (int64_t)((y + 1) % ly) * lx;
+        const int yd = (y + 1) % ly;
         // counts and nearest-neighbour pairs; lx is a multiple of 32 or the
         // tail is handled by the predicate, so every lane reaches the reduces
         for (int x0 = 0; x0 < lx; x0 += blockDim.x) {
             int x = x0 + threadIdx.x;
             unsigned int c0 = 0, c1 = 0, c2 = 0, pr = 0;
+            const int s = x < lx ? site_at<PACKED>(lat, lx, y, x) : -1;
             if (x < lx) {
-                int s = row[x];
                 c0 = s == 0; c1 = s == 1; c2 = s == 2;
-                if (s == 1) pr = (row[(x + 1) % lx] == 1) + (down[x] == 1);
+                if (s == 1) pr = (site_at<PACKED>(lat, lx, y, (x + 1) % lx) == 1) +
+                                 (site_at<PACKED>(lat, lx, yd, x) == 1);
             }
             c0 = __reduce_add_sync(0xffffffffu, c0);
             c1 = __reduce_add_sync(0xffffffffu, c1);
@@ -79,9 +110,9 @@ __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
             }
             for (int r = 1; r <= rmax; ++r) {
                 unsigned int gxv = 0, gyv = 0;
-                if (x < lx && row[x] == 1) {
-                    gxv = row[(x + r) % lx] == 1;
-                    gyv = lat[(int64_t)((y + r) % ly) * lx + x] == 1;
+                if (s == 1) {
+                    gxv = site_at<PACKED>(lat, lx, y, (x + r) % lx) == 1;
+                    gyv = site_at<PACKED>(lat, lx, (y + r) % ly, x) == 1;
                 }
                 gxv = __reduce_add_sync(0xffffffffu, gxv);
                 gyv = __reduce_add_sync(0xffffffffu, gyv);
@@ -132,11 +163,26 @@ cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned
 }
 
 cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
-                               unsigned long long *out, cudaStream_t s)
+                               unsigned long long *out, cudaStream_t s, bool packed)
 {
     int grid = ly < 152 * 8 ? ly : 152 * 8;
     size_t smem = sizeof(unsigned int) * (size_t)(4 + 2 * rmax);
-    observables_kernel<<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
+    if (packed) observables_kernel<true><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
+    else observables_kernel<false><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint8_t *bytes, uint32_t *words, int lx, int ly, cudaStream_t s)
+{
+    const int64_t nw = (int64_t)(lx >> 5) * ly;
+    pack_kernel<<<grid_for(nw, 256), 256, 0, s>>>(bytes, words, nw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const uint32_t *words, uint8_t *bytes, int lx, int ly, cudaStream_t s)
+{
+    const int64_t n = (int64_t)lx * ly;
+    unpack_kernel<<<grid_for(n, 256), 256, 0, s>>>(words, bytes, n);
     return cudaGetLastError();
 }
 

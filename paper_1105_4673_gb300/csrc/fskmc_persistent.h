@@ -25,6 +25,7 @@ struct PersistentRun {
     int64_t nwin;
     uint64_t w0, seed;
     uint32_t spin_limit;          // polls before a wait gives up
+    bool packed;                  // bit-packed lattice (spin-flip models)
 };
 
 struct PersistentState;  // device buffers and the captured CUDA graph

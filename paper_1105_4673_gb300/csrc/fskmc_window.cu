@@ -253,7 +253,7 @@ __device__ void copy_unwritten(const uint8_t *src, uint8_t *dst, int lx, int ly,
 // (counts times rates rounded to multiples of 2^-qshift), the class is the
 // first k with (w2 * lambda_int) >> 32 < P_k, and only the window clock
 // (lambda, waiting time, tau) is binary32 relative to the window start.
-template <int MODEL, typename CLK, bool PERSIST>
+template <int MODEL, typename CLK, bool PERSIST, bool PACKED>
 __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &G, int cx, int cy,
                                 int colour, uint32_t w, double hwin, uint64_t seed,
                                 const uint8_t *src, uint8_t *dst, int lane, bool *amb_out,
@@ -284,7 +284,13 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         int gy = Y0 - HW + by, gx = X0 - HW + bx;
         gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
         gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
-        box[i] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+        if (PACKED) {
+            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
+            const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
+            box[i] = (uint8_t)((wv >> (gx & 31)) & 1u);
+        } else {
+            box[i] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+        }
     }
     for (int i = lane; i < Lo.sitemask_words + Lo.slotmask_words; i += 32) sitemask[i] = 0u;
     if (lane < MAX_CLASSES) cnt[lane] = 0;
@@ -576,9 +582,35 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
 
     // Write back the write set: own sites, plus the halo ends of owned cross
     // bonds for the two-site models (columns in E windows, rows in O windows).
-    for (int i = lane; i < nsite; i += 32) {
-        int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
-        dst[(int64_t)(Y0 + lly) * lx + X0 + llx] = box[(lly + HW) * BW + llx + HW];
+    if (PACKED) {
+        // one row per lane; a word shared with other cells (cells narrower
+        // than 32 sites) is updated with atomics on this cell's bits only
+        uint32_t *dst32 = reinterpret_cast<uint32_t *>(dst);
+        for (int row = lane; row < qy; row += 32) {
+            const uint8_t *brow = box + (row + HW) * BW + HW - X0;
+            uint32_t *drow = dst32 + (int64_t)(Y0 + row) * (lx >> 5);
+            for (int x = X0; x < X0 + qx;) {
+                const int wi = x >> 5, xe = min(X0 + qx, (wi + 1) << 5);
+                uint32_t mask = 0u, bits = 0u;
+                for (int xx = x; xx < xe; ++xx) {
+                    const uint32_t b = 1u << (xx & 31);
+                    mask |= b;
+                    if (brow[xx]) bits |= b;
+                }
+                if (mask == 0xffffffffu) {
+                    drow[wi] = bits;
+                } else {
+                    atomicAnd(drow + wi, ~mask);
+                    atomicOr(drow + wi, bits);
+                }
+                x = xe;
+            }
+        }
+    } else {
+        for (int i = lane; i < nsite; i += 32) {
+            int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
+            dst[(int64_t)(Y0 + lly) * lx + X0 + llx] = box[(lly + HW) * BW + llx + HW];
+        }
     }
     if (TR::KB) {
         if (colour == 0) {
@@ -602,7 +634,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
 }
 
 // Plain engine: one launch per window, one warp per active cell of one replica.
-template <int MODEL, typename CLK>
+template <int MODEL, typename CLK, bool PACKED>
 __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -624,7 +656,7 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
         copy_unwritten<false>(src, dst, R.lx, R.ly, a.geom.qx, a.geom.qy, ncx2, ncy2, a.colour, lane);
     }
     bool amb = false, bad = false;
-    uint32_t e = cell_window<MODEL, CLK, false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cx,
+    uint32_t e = cell_window<MODEL, CLK, false, PACKED>(smem + (size_t)wib * smem_per_warp, R, a.geom, cx,
                                                 cy, a.colour, a.w, a.h, a.seed, src, dst, lane,
                                                 &amb, &bad);
     if (lane == 0) {
@@ -709,7 +741,7 @@ __device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target
     return true;
 }
 
-template <int MODEL, typename CLK>
+template <int MODEL, typename CLK, bool PACKED>
 __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -778,7 +810,7 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         if (!ok) break;
         if (active) {
             bool amb = false, bad = false;
-            uint32_t e = cell_window<MODEL, CLK, true>(wsm, R, P.geom, cx, cy, ccol,
+            uint32_t e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cx, cy, ccol,
                                                       P.w0 + (uint32_t)i, P.h[i], P.seed, cur,
                                                       nxt, lane, &amb, &bad);
             if (lane == 0) {
@@ -812,31 +844,35 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     size_t smem = (size_t)spw * wpb;
     int blocks = (nactive + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
-    if (fp32) {
-        auto kern = fs_window_kernel<MODEL, float>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
-    } else {
-        auto kern = fs_window_kernel<MODEL, double>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
+    void (*kern)(WindowArgs, int, int) = nullptr;
+    if constexpr (MODEL == ADSDES || MODEL == ISING) {
+        if (a.packed) kern = fp32 ? fs_window_kernel<MODEL, float, true> : fs_window_kernel<MODEL, double, true>;
     }
+    if (!kern) kern = fp32 ? fs_window_kernel<MODEL, float, false> : fs_window_kernel<MODEL, double, false>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
     return cudaGetLastError();
 }
 
 template <int MODEL>
-void *persistent_kernel_ptr(int fp32)
+void *persistent_kernel_ptr(int fp32, bool packed)
 {
-    return fp32 ? (void *)fs_persistent_kernel<MODEL, float> : (void *)fs_persistent_kernel<MODEL, double>;
+    if constexpr (MODEL == ADSDES || MODEL == ISING) {
+        if (packed)
+            return fp32 ? (void *)fs_persistent_kernel<MODEL, float, true>
+                        : (void *)fs_persistent_kernel<MODEL, double, true>;
+    }
+    return fp32 ? (void *)fs_persistent_kernel<MODEL, float, false>
+                : (void *)fs_persistent_kernel<MODEL, double, false>;
 }
 
-void *persistent_kernel_for(int model, int fp32)
+void *persistent_kernel_for(int model, int fp32, bool packed)
 {
     switch (model) {
-    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32);
-    case ISING: return persistent_kernel_ptr<ISING>(fp32);
-    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32);
-    case ZGB: return persistent_kernel_ptr<ZGB>(fp32);
+    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32, packed);
+    case ISING: return persistent_kernel_ptr<ISING>(fp32, packed);
+    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false);
+    case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false);
     }
     return nullptr;
 }
@@ -869,7 +905,7 @@ cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int nactive,
 // Device buffers of the persistent engine and the graph that launches it:
 // reset the per-cell epochs and the queue, then run the persistent kernel.
 struct PersistentState {
-    int model = -1, fp32 = -1, wpb = -1, grid = 0;
+    int model = -1, fp32 = -1, wpb = -1, grid = 0, packed = -1;
     PParams *d_params = nullptr;
     int32_t *d_epoch = nullptr;
     unsigned long long *d_queue = nullptr;  // [0] queue, [1] abort flag (low word)
@@ -929,10 +965,11 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         st->total_cells = run.total_cells;
     }
     // (Re)build the graph when the kernel variant or launch shape changes.
-    if (st->model != run.model || st->fp32 != run.fp32 || st->wpb != run.wpb) {
+    if (st->model != run.model || st->fp32 != run.fp32 || st->wpb != run.wpb ||
+        st->packed != (int)run.packed) {
         if (st->exec) { cudaGraphExecDestroy(st->exec); st->exec = nullptr; }
         if (st->graph) { cudaGraphDestroy(st->graph); st->graph = nullptr; }
-        void *kern = persistent_kernel_for(run.model, run.fp32);
+        void *kern = persistent_kernel_for(run.model, run.fp32, run.packed);
         const int spw = (int)window_smem_per_warp(run.model, run.qx, run.qy);
         const size_t smem = (size_t)spw * run.wpb;
         PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -957,6 +994,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         st->model = run.model;
         st->fp32 = run.fp32;
         st->wpb = run.wpb;
+        st->packed = (int)run.packed;
     }
     const size_t ncol = (size_t)run.nwin * (run.colour_per_replica ? run.nrep : 1);
     if (ncol > st->colour_cap) {

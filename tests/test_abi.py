@@ -81,3 +81,13 @@ def test_schedule_matches_oracle(lib, scheme, replica, w0):
     assert np.array_equal(col, ocol) and np.array_equal(h, oh)
     with pytest.raises(F.FskmcError):
         F.schedule(scheme, 0.07, 1.0)
+
+
+@pytest.mark.parametrize("lx,ly,model,q", [(64, 64, 3, (8, 8)),    # ZGB has three states
+                                           (48, 48, 1, (8, 8)),    # lx not a multiple of 32
+                                           (64, 64, 2, (8, 8))])   # diffusion: not a spin flip
+def test_bitpacked_validation(lib, lx, ly, model, q):
+    h = C.c_void_p()
+    st = lib.fskmc_create(C.byref(F.Lattice(lx, ly, 1)), model, C.byref(F._rates({})),
+                          F.CellShape(*q), None, C.byref(h))
+    assert st == F.EINVAL and not h.value

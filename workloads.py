@@ -22,7 +22,7 @@ WORKLOADS = {
                      seed=SEED_BASE + 0),
     "ising1024": dict(lx=1024, ly=1024, model="ISING",
                       rates=dict(ka=1.0, kd=1.0, betaJ=0.4407), q=(16, 16), scheme="LIE",
-                      dt=1.0, T=1000.0, coverage=0.5, seed=SEED_BASE + 1),
+                      dt=1.0, T=1000.0, coverage=0.5, bitpacked=True, seed=SEED_BASE + 1),
     "diffusion4096": dict(lx=4096, ly=4096, model="DIFFUSION",
                           rates=dict(ka=1.0, kd=1.0, betaJ=2.0, nu=10.0), q=(32, 32),
                           scheme="RANDOM_ORDER", dt=0.05, T=100.0, coverage=0.3,
