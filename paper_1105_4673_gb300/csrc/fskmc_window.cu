@@ -181,9 +181,39 @@ namespace {
 
 struct Layout {
     int BW, BH, nsite, s, SW;
-    int box_bytes, scls_bytes, sitemask_words, slotmask_words;
+    int box_bytes, scls_bytes, sitemask_words, slotmask_words, rowmask_words;
     int bytes;
 };
+
+// 8x8 bit-matrix transpose (row r = byte r, column c = bit c) by three
+// delta swaps.
+__device__ __forceinline__ uint64_t transpose8(uint64_t x)
+{
+    uint64_t t;
+    t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+    x = x ^ t ^ (t << 7);
+    t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+    x = x ^ t ^ (t << 14);
+    t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+    x = x ^ t ^ (t << 28);
+    return x;
+}
+
+// Slot-mask words of one lane from direction-major masks: D[d] bit t is slot
+// (site t, d) of the lane's 32 sites; the canonical layout puts slot (t, d)
+// at bit t*8 + d of the lane's 256-bit run (word t/4, byte t%4, bit d).
+__device__ __forceinline__ void store_slot_words(const uint32_t D[8], uint32_t *words, int lane)
+{
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint64_t m = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) m |= (uint64_t)((D[d] >> (8 * g)) & 0xFFu) << (8 * d);
+        m = transpose8(m);
+        words[(2 * g) * 32 + lane] = (uint32_t)m;
+        words[(2 * g + 1) * 32 + lane] = (uint32_t)(m >> 32);
+    }
+}
 
 // Per-warp shared memory: the cell and its halo (one byte per site), the
 // class code of every own site, membership masks ([mask][word][lane]),
@@ -202,8 +232,9 @@ __host__ __device__ inline Layout make_layout(int qx, int qy)
     L.scls_bytes = (L.nsite + 15) & ~15;
     L.sitemask_words = TR::KS * 32;
     L.slotmask_words = TR::KB * L.SW * 32;
+    L.rowmask_words = MODEL == ZGB ? 3 * L.BH : 0;
     L.bytes = L.box_bytes + L.scls_bytes + 4 * (L.sitemask_words + L.slotmask_words) +
-              4 * MAX_CLASSES + 8 * MAX_CLASSES + 8 * MAX_CLASSES;
+              4 * MAX_CLASSES + 8 * MAX_CLASSES + 8 * MAX_CLASSES + 4 * L.rowmask_words;
     L.bytes = (L.bytes + 15) & ~15;
     return L;
 }
@@ -271,6 +302,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     uint32_t *slotmask = sitemask + Lo.sitemask_words;
     int *cnt = reinterpret_cast<int *>(slotmask + Lo.slotmask_words);
     double *dcnt = reinterpret_cast<double *>(cnt + MAX_CLASSES);
+    uint32_t *rowm = reinterpret_cast<uint32_t *>(dcnt + 2 * MAX_CLASSES);
 
     const int lx = R.lx, ly = R.ly;
     const int m = cy * R.ncx + cx;
@@ -278,48 +310,115 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     const int BW = Lo.BW, BH = Lo.BH, SW = Lo.SW, nsite = Lo.nsite;
     const int NL = (nsite + 31) >> 5;  // lanes that own sites
 
-    // Stage the cell and its halo (periodic wrap) from the window-start state.
-    for (int i = lane; i < BW * BH; i += 32) {
-        int by = i / BW, bx = i - by * BW;
-        int gy = Y0 - HW + by, gx = X0 - HW + bx;
-        gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-        gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
-        if (PACKED) {
-            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
-            const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
-            box[i] = (uint8_t)((wv >> (gx & 31)) & 1u);
-        } else {
-            box[i] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+    // ZGB with 32-wide cells: rows are staged one per step so that warp
+    // ballots give each row's state masks for the bit-parallel class build.
+    const bool zrow = (MODEL == ZGB) && !PACKED && qx == 32;
+    if (zrow) {
+        for (int by = 0; by < BH; ++by) {
+            int gy = Y0 - HW + by;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            const uint8_t *srow = src + (int64_t)gy * lx;
+            const uint8_t v = ld_site<PERSIST>(srow + X0 + lane);
+            box[by * BW + HW + lane] = v;
+            const uint32_t me = __ballot_sync(0xffffffffu, v == 0);
+            const uint32_t ma = __ballot_sync(0xffffffffu, v == 1);
+            const uint32_t mb = __ballot_sync(0xffffffffu, v == 2);
+            if (lane == 0) { rowm[by] = me; rowm[BH + by] = ma; rowm[2 * BH + by] = mb; }
+            if (lane == 1) box[by * BW] = ld_site<PERSIST>(srow + (X0 == 0 ? lx - 1 : X0 - 1));
+            if (lane == 2) box[by * BW + BW - 1] = ld_site<PERSIST>(srow + (X0 + 32 == lx ? 0 : X0 + 32));
+        }
+    } else {
+        // Stage the cell and its halo (periodic wrap) from the window-start state.
+        for (int i = lane; i < BW * BH; i += 32) {
+            int by = i / BW, bx = i - by * BW;
+            int gy = Y0 - HW + by, gx = X0 - HW + bx;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+            if (PACKED) {
+                const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
+                const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
+                box[i] = (uint8_t)((wv >> (gx & 31)) & 1u);
+            } else {
+                box[i] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+            }
         }
     }
     for (int i = lane; i < Lo.sitemask_words + Lo.slotmask_words; i += 32) sitemask[i] = 0u;
     if (lane < MAX_CLASSES) cnt[lane] = 0;
     __syncwarp();
 
-    // Class build: each lane classifies its own run of 32 sites and their slots.
-    const int i0 = lane * 32;
-    for (int t = 0; t < 32; ++t) {
-        int i = i0 + t;
-        if (i >= nsite) break;
-        int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
-        int p = (lly + HW) * BW + llx + HW;
-        int k = site_class<MODEL>(box, BW, p);
-        scls[i] = (uint8_t)k;
-        if (k >= 0) sitemask[mask_of<MODEL>(k) * 32 + lane] |= 1u << t;
-        if (TR::KB) {
+    if (zrow) {
+        // Bit-parallel class build, one cell row per lane: site classes are
+        // the row's empty / A masks; slot classes compare each site with its
+        // neighbour in every direction (N, E, S, W outward, then inward), with
+        // the ownership rule as masks, and are transposed into the canonical
+        // site-major slot layout.
+        if (lane < qy) {
+            const int yb = lane + HW;
+            const uint32_t e = rowm[yb], a = rowm[BH + yb], b = rowm[2 * BH + yb];
+            const int hl = box[yb * BW], hr = box[yb * BW + BW - 1];
+            uint32_t tE[4], tA[4], tB[4];
+            tE[0] = rowm[yb - 1]; tA[0] = rowm[BH + yb - 1]; tB[0] = rowm[2 * BH + yb - 1];
+            tE[2] = rowm[yb + 1]; tA[2] = rowm[BH + yb + 1]; tB[2] = rowm[2 * BH + yb + 1];
+            tE[1] = (e >> 1) | ((uint32_t)(hr == 0) << 31);
+            tA[1] = (a >> 1) | ((uint32_t)(hr == 1) << 31);
+            tB[1] = (b >> 1) | ((uint32_t)(hr == 2) << 31);
+            tE[3] = (e << 1) | (uint32_t)(hl == 0);
+            tA[3] = (a << 1) | (uint32_t)(hl == 1);
+            tB[3] = (b << 1) | (uint32_t)(hl == 2);
+            const bool ew = colour == 0;  // horizontal cross bonds belong to E cells
+            uint32_t own[8];
+            own[0] = (lane > 0 || !ew) ? ~0u : 0u;
+            own[1] = ew ? ~0u : 0x7FFFFFFFu;
+            own[2] = (lane < qy - 1 || !ew) ? ~0u : 0u;
+            own[3] = ew ? ~0u : 0xFFFFFFFEu;
+            own[4] = (lane == 0 && !ew) ? ~0u : 0u;
+            own[5] = ew ? 0x80000000u : 0u;
+            own[6] = (lane == qy - 1 && !ew) ? ~0u : 0u;
+            own[7] = ew ? 1u : 0u;
+            uint32_t D1[8], D2[8];
 #pragma unroll
             for (int d = 0; d < 8; ++d) {
-                if (!slot_owned(llx, lly, d, qx, qy, colour)) continue;
-                int dir = d & 3;
-                int pn = p + dir_dy(dir) * BW + dir_dx(dir);
-                int kb = (d < 4) ? slot_class<MODEL>(box, BW, p, pn) : slot_class<MODEL>(box, BW, pn, p);
-                if (kb < 0) continue;
-                int bit = t * 8 + d;
-                slotmask[(mask_of<MODEL>(kb) * SW + (bit >> 5)) * 32 + lane] |= 1u << (bit & 31);
+                const int dir = d & 3;
+                D1[d] = e & tE[dir] & own[d];                             // B2 adsorbs: both empty
+                D2[d] = ((a & tB[dir]) | (b & tA[dir])) & own[d];         // A + B react
+            }
+            store_slot_words(D1, slotmask + (mask_of<MODEL>(1) * SW) * 32, lane);
+            store_slot_words(D2, slotmask + (mask_of<MODEL>(2) * SW) * 32, lane);
+            sitemask[mask_of<MODEL>(0) * 32 + lane] = e;
+            sitemask[mask_of<MODEL>(3) * 32 + lane] = a;
+            uint8_t *srow = scls + lane * 32;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t)
+                srow[t] = ((e >> t) & 1u) ? 0 : (((a >> t) & 1u) ? 3 : 0xFF);
+        }
+        __syncwarp();
+    } else {
+        // Class build: each lane classifies its own run of 32 sites and their slots.
+        const int i0 = lane * 32;
+        for (int t = 0; t < 32; ++t) {
+            int i = i0 + t;
+            if (i >= nsite) break;
+            int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
+            int p = (lly + HW) * BW + llx + HW;
+            int k = site_class<MODEL>(box, BW, p);
+            scls[i] = (uint8_t)k;
+            if (k >= 0) sitemask[mask_of<MODEL>(k) * 32 + lane] |= 1u << t;
+            if (TR::KB) {
+    #pragma unroll
+                for (int d = 0; d < 8; ++d) {
+                    if (!slot_owned(llx, lly, d, qx, qy, colour)) continue;
+                    int dir = d & 3;
+                    int pn = p + dir_dy(dir) * BW + dir_dx(dir);
+                    int kb = (d < 4) ? slot_class<MODEL>(box, BW, p, pn) : slot_class<MODEL>(box, BW, pn, p);
+                    if (kb < 0) continue;
+                    int bit = t * 8 + d;
+                    slotmask[(mask_of<MODEL>(kb) * SW + (bit >> 5)) * 32 + lane] |= 1u << (bit & 31);
+                }
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         int c = 0;

@@ -31,6 +31,8 @@ GEOMS = [
     ("ZGB", 64, 64, (8, 8)),
     ("ZGB", 8, 8, (2, 2)),
     ("ZGB", 96, 64, (16, 32)),
+    ("ZGB", 128, 64, (32, 32)),
+    ("ZGB", 64, 96, (32, 16)),
 ]
 
 
