@@ -199,6 +199,22 @@ __device__ __forceinline__ uint64_t transpose8(uint64_t x)
     return x;
 }
 
+// Per-site count n of occupied nearest neighbours (0..4) of a row of 32
+// sites, from the occupancy masks of its four neighbours, as bit planes; eq[v]
+// is the mask of sites with n == v.
+__device__ __forceinline__ void count_eq(uint32_t up, uint32_t right, uint32_t down, uint32_t left,
+                                         uint32_t eq[5])
+{
+    const uint32_t s1 = up ^ down, c1 = up & down, s2 = right ^ left, c2 = right & left;
+    const uint32_t b0 = s1 ^ s2, k0 = s1 & s2;
+    const uint32_t b1 = c1 ^ c2 ^ k0, b2 = (c1 & c2) | (k0 & (c1 ^ c2));
+    eq[0] = ~b0 & ~b1 & ~b2;
+    eq[1] = b0 & ~b1 & ~b2;
+    eq[2] = ~b0 & b1 & ~b2;
+    eq[3] = b0 & b1 & ~b2;
+    eq[4] = ~b0 & ~b1 & b2;
+}
+
 // Slot-mask words of one lane from direction-major masks: D[d] bit t is slot
 // (site t, d) of the lane's 32 sites; the canonical layout puts slot (t, d)
 // at bit t*8 + d of the lane's 256-bit run (word t/4, byte t%4, bit d).
@@ -232,7 +248,7 @@ __host__ __device__ inline Layout make_layout(int qx, int qy)
     L.scls_bytes = (L.nsite + 15) & ~15;
     L.sitemask_words = TR::KS * 32;
     L.slotmask_words = TR::KB * L.SW * 32;
-    L.rowmask_words = MODEL == ZGB ? 3 * L.BH : 0;
+    L.rowmask_words = MODEL == ZGB ? 3 * L.BH : (MODEL == DIFFUSION ? L.BH : 0);
     L.bytes = L.box_bytes + L.scls_bytes + 4 * (L.sitemask_words + L.slotmask_words) +
               4 * MAX_CLASSES + 8 * MAX_CLASSES + 8 * MAX_CLASSES + 4 * L.rowmask_words;
     L.bytes = (L.bytes + 15) & ~15;
@@ -313,7 +329,25 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     // ZGB with 32-wide cells: rows are staged one per step so that warp
     // ballots give each row's state masks for the bit-parallel class build.
     const bool zrow = (MODEL == ZGB) && !PACKED && qx == 32;
-    if (zrow) {
+    const bool drow = (MODEL == DIFFUSION) && qx == 32;
+    if (drow) {
+        for (int by = 0; by < BH; ++by) {
+            int gy = Y0 - HW + by;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            const uint8_t *srow = src + (int64_t)gy * lx;
+            const uint8_t v = ld_site<PERSIST>(srow + X0 + lane);
+            box[by * BW + HW + lane] = v;
+            const uint32_t mo = __ballot_sync(0xffffffffu, v == 1);
+            if (lane == 0) rowm[by] = mo;
+            if (lane >= 1 && lane <= 4) {
+                // halo columns x = -2, -1, 32, 33
+                const int hx = lane <= 2 ? lane - 3 : 32 + (lane - 3);
+                int gx = X0 + hx;
+                gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+                box[by * BW + HW + hx] = ld_site<PERSIST>(srow + gx);
+            }
+        }
+    } else if (zrow) {
         for (int by = 0; by < BH; ++by) {
             int gy = Y0 - HW + by;
             gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
@@ -347,7 +381,74 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     if (lane < MAX_CLASSES) cnt[lane] = 0;
     __syncwarp();
 
-    if (zrow) {
+    if (drow) {
+        // Bit-parallel class build, one cell row per lane: every site's
+        // occupied-neighbour count n comes from bit-sliced adders over the
+        // neighbour rows; site classes are 5 sigma + n; a hop slot's class is
+        // 10 + n(origin) when the origin is occupied and the target empty, its
+        // origin being the site (outward) or the halo site (inward).
+        if (lane < qy) {
+            const int yb = lane + HW;
+            const uint8_t *b0 = box + yb * BW + HW;          // this row, x = 0
+            const uint8_t *bu = b0 - BW, *bd = b0 + BW;      // rows above and below
+            const uint32_t o = rowm[yb], oN = rowm[yb - 1], oS = rowm[yb + 1];
+            const uint32_t oNN = rowm[yb - 2], oSS = rowm[yb + 2];
+            const uint32_t hl1 = b0[-1] == 1, hl2 = b0[-2] == 1, hr1 = b0[32] == 1, hr2 = b0[33] == 1;
+            uint32_t oT[4];
+            oT[0] = oN;
+            oT[1] = (o >> 1) | (hr1 << 31);
+            oT[2] = oS;
+            oT[3] = (o << 1) | hl1;
+            uint32_t eq[5];
+            count_eq(oN, oT[1], oS, oT[3], eq);
+            // the counts of the inward origins: the rows above / below the
+            // cell (whole rows) and the halo sites left and right of this row
+            uint32_t eqN[5], eqS[5];
+            {
+                const uint32_t rl = (oN << 1) | (uint32_t)(bu[-1] == 1), rr = (oN >> 1) | ((uint32_t)(bu[32] == 1) << 31);
+                count_eq(oNN, rr, o, rl, eqN);
+                const uint32_t sl = (oS << 1) | (uint32_t)(bd[-1] == 1), sr = (oS >> 1) | ((uint32_t)(bd[32] == 1) << 31);
+                count_eq(o, sr, oSS, sl, eqS);
+            }
+            const int nW = (int)hl2 + (int)(o & 1u) + (bu[-1] == 1) + (bd[-1] == 1);  // origin x = -1
+            const int nE = (int)(o >> 31) + (int)hr2 + (bu[32] == 1) + (bd[32] == 1);  // origin x = 32
+            const bool ew = colour == 0;
+            uint32_t own[8];
+            own[0] = (lane > 0 || !ew) ? ~0u : 0u;
+            own[1] = ew ? ~0u : 0x7FFFFFFFu;
+            own[2] = (lane < qy - 1 || !ew) ? ~0u : 0u;
+            own[3] = ew ? ~0u : 0xFFFFFFFEu;
+            own[4] = (lane == 0 && !ew) ? ~0u : 0u;
+            own[5] = ew ? 0x80000000u : 0u;
+            own[6] = (lane == qy - 1 && !ew) ? ~0u : 0u;
+            own[7] = ew ? 1u : 0u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t D[8];
+#pragma unroll
+                for (int d = 0; d < 4; ++d) D[d] = o & ~oT[d] & eq[c] & own[d];  // outward
+                D[4] = ~o & oN & eqN[c] & own[4];                                  // from the row above
+                D[5] = ~o & oT[1] & (nE == c ? 0x80000000u : 0u) & own[5];        // from x = 32
+                D[6] = ~o & oS & eqS[c] & own[6];                                  // from the row below
+                D[7] = ~o & oT[3] & (nW == c ? 1u : 0u) & own[7];                  // from x = -1
+                store_slot_words(D, slotmask + (mask_of<MODEL>(10 + c) * SW) * 32, lane);
+            }
+#pragma unroll
+            for (int n = 0; n < 5; ++n) {
+                sitemask[n * 32 + lane] = ~o & eq[n];
+                sitemask[(5 + n) * 32 + lane] = o & eq[n];
+            }
+            uint8_t *srow = scls + lane * 32;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) {
+                int n = 0;
+#pragma unroll
+                for (int v = 1; v < 5; ++v) n += ((eq[v] >> t) & 1u) * v;
+                srow[t] = (uint8_t)(5 * ((o >> t) & 1u) + n);
+            }
+        }
+        __syncwarp();
+    } else if (zrow) {
         // Bit-parallel class build, one cell row per lane: site classes are
         // the row's empty / A masks; slot classes compare each site with its
         // neighbour in every direction (N, E, S, W outward, then inward), with

@@ -28,6 +28,8 @@ GEOMS = [
     ("ISING", 128, 64, (32, 32)),
     ("DIFFUSION", 48, 48, (8, 8)),
     ("DIFFUSION", 16, 24, (4, 6)),
+    ("DIFFUSION", 64, 64, (32, 32)),
+    ("DIFFUSION", 128, 96, (32, 16)),
     ("ZGB", 64, 64, (8, 8)),
     ("ZGB", 8, 8, (2, 2)),
     ("ZGB", 96, 64, (16, 32)),
