@@ -30,9 +30,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fskmc_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 
-MODELS = {"ADSDES": 0, "ISING": 1, "DIFFUSION": 2, "ZGB": 3}
+MODELS = {"ADSDES": 0, "ISING": 1, "DIFFUSION": 2, "ZGB": 3, "ISING1D": 4}
 SCHEMES = {"LIE": 0, "STRANG": 1, "RANDOM": 2, "RANDOM_ORDER": 3}
-NCLASS = {0: 10, 1: 10, 2: 15, 3: 4}
+NCLASS = {0: 10, 1: 10, 2: 15, 3: 4, 4: 6}
 
 
 def build(force: bool = False) -> str:
@@ -62,7 +62,7 @@ def lib():
         u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
         i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
         L.orc_philox.argtypes = [u32p, u32p, u32p]
-        L.orc_rates.argtypes = [C.c_int] + [C.c_double] * 6 + [f64p]
+        L.orc_rates.argtypes = [C.c_int] + [C.c_double] * 7 + [f64p]
         L.orc_rates.restype = C.c_int
         L.orc_init_bernoulli.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_double, C.c_uint32, u8p]
         L.orc_init_bump.argtypes = [C.c_int, C.c_int, C.c_uint64, C.c_double, C.c_double,
@@ -104,9 +104,10 @@ def lib():
 
 
 def _rates6(rates: dict) -> np.ndarray:
+    """{ka, kd, betaJ, nu, yA, kr, betah} as the C side reads them."""
     return np.array([rates.get("ka", 1.0), rates.get("kd", 1.0), rates.get("betaJ", 0.0),
-                     rates.get("nu", 0.0), rates.get("yA", 0.0), rates.get("kr", 0.0)],
-                    dtype=np.float64)
+                     rates.get("nu", 0.0), rates.get("yA", 0.0), rates.get("kr", 0.0),
+                     rates.get("betah", 0.0)], dtype=np.float64)
 
 
 def _model(model) -> int:

@@ -46,6 +46,8 @@ def events(lx, ly, model, rates, S=None):
       ADSDES     c(x) = ka (1 - s_x) + kd s_x exp(-beta U), U = J sum_nn s_y
       ISING      c(x) = ka (1 - s_x) + kd s_x exp(-beta U), U = K sum_nn s_y - h,
                  K = 4J, h = 2K (zero spin field)
+      ISING1D    the same on a ring (ly = 1, neighbours x-1 and x+1 only),
+                 beta K = betaJ and beta h = betah given freely (Section 7)
       DIFFUSION  ADSDES flips, plus a hop x->y (|x-y| = 1) of a particle at x to
                  an empty y with rate nu exp(-beta J sum_{z nn x} s_z)
       ZGB        Table COrates with A = the single-site adsorber, B = the
@@ -61,15 +63,18 @@ def events(lx, ly, model, rates, S=None):
     if S is None:
         S = decode(lx, ly, base)
     ka, kd, bJ = rates.get("ka", 1.0), rates.get("kd", 1.0), rates.get("betaJ", 0.0)
-    nn_occ = np.stack([sum((S[:, _nb(lx, ly, i, d)] == 1).astype(np.int64) for d in range(4))
+    dirs = (1, 3) if model == "ISING1D" else range(4)
+    nn_occ = np.stack([sum((S[:, _nb(lx, ly, i, d)] == 1).astype(np.int64) for d in dirs)
                        for i in range(N)], axis=1)
     out = []
-    if model in ("ADSDES", "ISING", "DIFFUSION"):
+    if model in ("ADSDES", "ISING", "DIFFUSION", "ISING1D"):
         for i in range(N):
             s = S[:, i].astype(np.float64)
             if model == "ISING":
                 K, h = 4.0 * bJ, 8.0 * bJ  # beta*K and beta*h
                 U = K * nn_occ[:, i] - h
+            elif model == "ISING1D":
+                U = bJ * nn_occ[:, i] - rates.get("betah", 0.0)
             else:
                 U = bJ * nn_occ[:, i]
             c = ka * (1 - s) + kd * s * np.exp(-U)
@@ -210,6 +215,18 @@ def gibbs_ising(lx, ly, betaJ):
             pair += S[:, i] * S[:, _nb(lx, ly, i, d)]
     bK, bh = 4.0 * betaJ, 8.0 * betaJ
     logw = bK * pair - bh * S.sum(axis=1)
+    w = np.exp(logw - logw.max())
+    return w / w.sum()
+
+
+def gibbs_ising1d(lx, betaK, betah, ka=1.0, kd=1.0):
+    """Stationary weights of the ring's adsorption/desorption dynamics:
+    pi(s) proportional to (ka/kd)^N1 exp(beta K sum_x s_x s_{x+1} - beta h N1)
+    (detailed balance of the ISING1D rates, written per configuration)."""
+    S = decode(lx, 1, 2).astype(np.float64)
+    pair = sum(S[:, i] * S[:, (i + 1) % lx] for i in range(lx))
+    n1 = S.sum(axis=1)
+    logw = betaK * pair + (np.log(ka / kd) - betah) * n1
     w = np.exp(logw - logw.max())
     return w / w.sum()
 

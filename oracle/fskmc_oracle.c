@@ -61,6 +61,7 @@
 #define ORC_ISING 1
 #define ORC_DIFFUSION 2
 #define ORC_ZGB 3
+#define ORC_ISING1D 4
 
 #define ORC_LIE 0
 #define ORC_STRANG 1
@@ -132,6 +133,11 @@ typedef struct {
  *          example 2): classes 0-9 as ADSDES; 10+n is a directed slot whose
  *          origin is occupied with n occupied neighbours and whose target is
  *          empty, rate nu*exp(-betaJ*n).
+ *  ISING1D (the 1D Ising benchmark of Section 7 on a ring, ly = 1, with
+ *          H = -K sum sigma(x) sigma(x+1) + h sum sigma(x), betaJ = beta K,
+ *          betah = beta h; detailed balance as for ISING): class 3*sigma + n,
+ *          n = occupied east/west neighbours; r(0,n) = ka,
+ *          r(1,n) = kd*exp(-(beta K n - beta h)).
  *  ZGB     (Table COrates; states 0 empty, 1 A, 2 B): 0 A adsorbs on an empty
  *          site (yA); 1 B2 adsorbs on a directed slot with both ends empty
  *          ((1-yA)/4); 2 A+B react on a directed slot holding (A,B) or (B,A)
@@ -139,10 +145,16 @@ typedef struct {
  * Returns the number of classes, or -1 for an unknown model.
  */
 int orc_rates(int model, double ka, double kd, double betaJ, double nu,
-              double yA, double kr, double *r)
+              double yA, double kr, double betah, double *r)
 {
     int n;
     switch (model) {
+    case ORC_ISING1D:
+        for (n = 0; n < 3; n++) {
+            r[n] = ka;
+            r[3 + n] = kd * exp(-(betaJ * (double)n - betah));
+        }
+        return 6;
     case ORC_ADSDES:
         for (n = 0; n < 5; n++) {
             r[n] = ka;
@@ -173,17 +185,26 @@ int orc_rates(int model, double ka, double kd, double betaJ, double nu,
 }
 
 static int sys_init(sys_t *S, int lx, int ly, int qx, int qy, int model,
-                    const double *rates6)
+                    const double *rates7)
 {
     memset(S, 0, sizeof(*S));
     S->lx = lx; S->ly = ly; S->qx = qx; S->qy = qy;
     S->ncx = qx > 0 ? lx / qx : 0;
     S->ncy = qy > 0 ? ly / qy : 0;
     S->model = model;
-    S->nclass = orc_rates(model, rates6[0], rates6[1], rates6[2], rates6[3],
-                          rates6[4], rates6[5], S->r);
+    S->nclass = orc_rates(model, rates7[0], rates7[1], rates7[2], rates7[3],
+                          rates7[4], rates7[5], rates7[6], S->r);
     S->slots = (model == ORC_DIFFUSION || model == ORC_ZGB);
     return S->nclass > 0 ? 0 : -1;
+}
+
+/* Cell geometry: lx % 2qx == 0 and ly % 2qy == 0 (a checkerboard of
+ * cells); the 1D ring has ly == qy == 1 (cells alternate along x). */
+static int geometry_ok(int model, int lx, int ly, int qx, int qy)
+{
+    if (qx < 1 || qy < 1 || lx % (2 * qx)) return 0;
+    if (model == ORC_ISING1D) return ly == 1 && qy == 1;
+    return ly % (2 * qy) == 0;
 }
 
 static int wrap(int a, int n)
@@ -233,6 +254,8 @@ static int site_class(const view_t *v, int x, int y)
 {
     int s = vget(v, sidx(v->S, x, y));
     switch (v->S->model) {
+    case ORC_ISING1D:
+        return 3 * s + (vget(v, sidx(v->S, x - 1, y)) == 1) + (vget(v, sidx(v->S, x + 1, y)) == 1);
     case ORC_ADSDES:
     case ORC_ISING:
     case ORC_DIFFUSION:
@@ -334,6 +357,7 @@ static void apply_member(view_t *v, const member_t *mb, int k)
     switch (S->model) {
     case ORC_ADSDES:
     case ORC_ISING:
+    case ORC_ISING1D:
         vset(v, io, 1 - vget(v, io));
         break;
     case ORC_DIFFUSION:
@@ -547,7 +571,7 @@ int64_t orc_schedule(int scheme, double dt, double T, uint64_t seed, uint32_t re
 
 /* ------------------------------------------------------------------------ */
 /* Exported entry points (argument meaning is in oracle/__init__.py).       */
-/* rates6 = {ka, kd, betaJ, nu, yA, kr}.                                    */
+/* rates7 = {ka, kd, betaJ, nu, yA, kr}.                                    */
 /* ------------------------------------------------------------------------ */
 
 /* Bernoulli(p) initial state: site i of replica rep is 1 iff word 0 of
@@ -605,14 +629,14 @@ void orc_init_bump(int lx, int ly, uint64_t seed, double amp, double width,
  * workload (ncx*ncy, may be NULL) receives each cell's event count in its
  * latest window. Returns 0, or -1 on invalid arguments.
  */
-int orc_fs_run(int lx, int ly, int qx, int qy, int model, const double *rates6,
+int orc_fs_run(int lx, int ly, int qx, int qy, int model, const double *rates7,
                int scheme, double dt, double T, uint64_t seed, uint32_t rep,
                uint32_t *w, int order, uint8_t *lat, uint64_t *stats_out,
                int32_t *workload)
 {
     sys_t S;
-    if (qx < 1 || qy < 1 || lx % (2 * qx) || ly % (2 * qy)) return -1;
-    if (sys_init(&S, lx, ly, qx, qy, model, rates6)) return -1;
+    if (!geometry_ok(model, lx, ly, qx, qy)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
     int64_t nw = orc_schedule(scheme, dt, T, seed, rep, *w, NULL, NULL, 0);
     if (nw < 0) return -1;
     int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nw + 1));
@@ -637,14 +661,14 @@ int orc_fs_run(int lx, int ly, int qx, int qy, int model, const double *rates6,
 /* One window of colour col and length h at global index w (for per-window
  * comparisons). amb_cells (ncx*ncy, may be NULL) gets 1 for cells whose
  * window was flagged ambiguous. */
-int orc_window(int lx, int ly, int qx, int qy, int model, const double *rates6,
+int orc_window(int lx, int ly, int qx, int qy, int model, const double *rates7,
                int col, double h, uint32_t w, uint64_t seed, uint32_t rep,
                uint8_t *lat, uint64_t *stats_out, int32_t *workload,
                int32_t *amb_cells)
 {
     sys_t S;
-    if (qx < 1 || qy < 1 || lx % (2 * qx) || ly % (2 * qy)) return -1;
-    if (sys_init(&S, lx, ly, qx, qy, model, rates6)) return -1;
+    if (!geometry_ok(model, lx, ly, qx, qy)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
     work_t W;
     if (work_init(&W, &S)) { work_free(&W); return -1; }
     size_t N = (size_t)lx * ly;
@@ -675,11 +699,11 @@ int orc_window(int lx, int ly, int qx, int qy, int model, const double *rates6,
  * (e lo, e hi, 0, rep | 1<<24). The total rate is recounted every event
  * (the direct method, O(N) per event). Returns the number of events.
  */
-int64_t orc_ssa_run(int lx, int ly, int model, const double *rates6, double T,
+int64_t orc_ssa_run(int lx, int ly, int model, const double *rates7, double T,
                     uint64_t seed, uint32_t rep, uint8_t *lat)
 {
     sys_t S;
-    if (sys_init(&S, lx, ly, lx, ly, model, rates6)) return -1;
+    if (sys_init(&S, lx, ly, lx, ly, model, rates7)) return -1;
     size_t N = (size_t)lx * ly;
     member_t *mb = (member_t *)malloc(sizeof(member_t) * (N * 5 + 1));
     uint32_t *stamp = (uint32_t *)calloc(N, sizeof(uint32_t));
@@ -715,11 +739,11 @@ int64_t orc_ssa_run(int lx, int ly, int model, const double *rates6, double T,
 
 /* Total rate lambda(sigma) of Eq. totalrate over the whole lattice, and the
  * per-class counts (whole-lattice candidate set as in orc_ssa_run). */
-double orc_total_rate(int lx, int ly, int model, const double *rates6,
+double orc_total_rate(int lx, int ly, int model, const double *rates7,
                       const uint8_t *lat, int64_t *counts)
 {
     sys_t S;
-    if (sys_init(&S, lx, ly, lx, ly, model, rates6)) return -1.0;
+    if (sys_init(&S, lx, ly, lx, ly, model, rates7)) return -1.0;
     size_t N = (size_t)lx * ly;
     uint32_t *stamp = (uint32_t *)calloc(N, sizeof(uint32_t));
     view_t v = {&S, lat, (uint8_t *)lat, stamp, 1};
@@ -743,12 +767,12 @@ double orc_total_rate(int lx, int ly, int model, const double *rates6,
 /* Members a cell owns in a window of colour col (for the partition tests):
  * origin and target site indices and class of each, canonical order. */
 int orc_cell_members(int lx, int ly, int qx, int qy, int model,
-                     const double *rates6, const uint8_t *lat, int m, int col,
+                     const double *rates7, const uint8_t *lat, int m, int col,
                      int32_t *origin, int32_t *target, int32_t *kind,
                      int32_t *cls)
 {
     sys_t S;
-    if (sys_init(&S, lx, ly, qx, qy, model, rates6)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
     size_t N = (size_t)lx * ly;
     uint32_t *stamp = (uint32_t *)calloc(N, sizeof(uint32_t));
     member_t *mb = (member_t *)malloc(sizeof(member_t) * (size_t)(9 * qx * qy + 8));
@@ -769,7 +793,7 @@ int orc_cell_writeset(int lx, int ly, int qx, int qy, int model, int m, int col,
                       int32_t *out)
 {
     sys_t S;
-    double r6[6] = {1, 1, 0, 1, 0.5, 1};
+    double r6[7] = {1, 1, 0, 1, 0.5, 1, 0};
     if (sys_init(&S, lx, ly, qx, qy, model, r6)) return -1;
     int *ws = (int *)malloc(sizeof(int) * (size_t)(qx * qy + 2 * (qx + qy) + 8));
     int n = cell_writeset(&S, m % S.ncx, m / S.ncx, col, ws);
@@ -782,7 +806,8 @@ int orc_cell_writeset(int lx, int ly, int qx, int qy, int model, int m, int col,
  * Observables of Section 7 as exact integer sums: counts[s] = sites in
  * state s (s < 3); pairs = nearest-neighbour bonds (each once) with both
  * ends in state 1; gx[r-1], gy[r-1] = sum over sites of
- * [sigma(x)=1][sigma(x + r e)=1] along x and y, r = 1..rmax.
+ * [sigma(x)=1][sigma(x + r e)=1] along x and y, r = 1..rmax. A ring (ly = 1)
+ * has no vertical bonds: its vertical terms are 0.
  */
 void orc_observables(int lx, int ly, const uint8_t *lat, int rmax,
                      int64_t *counts, int64_t *pairs, int64_t *gx, int64_t *gy)
@@ -796,10 +821,10 @@ void orc_observables(int lx, int ly, const uint8_t *lat, int rmax,
             if (s < 3) counts[s]++;
             if (s != 1) continue;
             *pairs += lat[(size_t)y * lx + (x + 1) % lx] == 1;
-            *pairs += lat[(size_t)((y + 1) % ly) * lx + x] == 1;
+            if (ly > 1) *pairs += lat[(size_t)((y + 1) % ly) * lx + x] == 1;
             for (int r = 1; r <= rmax; r++) {
                 gx[r - 1] += lat[(size_t)y * lx + (x + r) % lx] == 1;
-                gy[r - 1] += lat[(size_t)((y + r) % ly) * lx + x] == 1;
+                if (ly > 1) gy[r - 1] += lat[(size_t)((y + r) % ly) * lx + x] == 1;
             }
         }
 }
@@ -807,7 +832,7 @@ void orc_observables(int lx, int ly, const uint8_t *lat, int rmax,
 /* M independent FS runs from the same initial state (replica r = 0..M-1,
  * window index from 0); final states into out[M*lx*ly]. */
 int orc_fs_ensemble(int lx, int ly, int qx, int qy, int model,
-                    const double *rates6, int scheme, double dt, double T,
+                    const double *rates7, int scheme, double dt, double T,
                     uint64_t seed, int M, const uint8_t *init, uint8_t *out)
 {
     size_t N = (size_t)lx * ly;
@@ -816,7 +841,7 @@ int orc_fs_ensemble(int lx, int ly, int qx, int qy, int model,
         uint32_t w = 0;
         uint64_t st[3] = {0, 0, 0};
         memcpy(lat, init, N);
-        if (orc_fs_run(lx, ly, qx, qy, model, rates6, scheme, dt, T, seed,
+        if (orc_fs_run(lx, ly, qx, qy, model, rates7, scheme, dt, T, seed,
                        (uint32_t)r, &w, 0, lat, st, NULL))
             return -1;
     }
@@ -824,14 +849,14 @@ int orc_fs_ensemble(int lx, int ly, int qx, int qy, int model,
 }
 
 /* M independent serial SSA runs from the same initial state. */
-int orc_ssa_ensemble(int lx, int ly, int model, const double *rates6, double T,
+int orc_ssa_ensemble(int lx, int ly, int model, const double *rates7, double T,
                      uint64_t seed, int M, const uint8_t *init, uint8_t *out)
 {
     size_t N = (size_t)lx * ly;
     for (int r = 0; r < M; r++) {
         uint8_t *lat = out + (size_t)r * N;
         memcpy(lat, init, N);
-        if (orc_ssa_run(lx, ly, model, rates6, T, seed, (uint32_t)r, lat) < 0)
+        if (orc_ssa_run(lx, ly, model, rates7, T, seed, (uint32_t)r, lat) < 0)
             return -1;
     }
     return 0;
@@ -843,13 +868,13 @@ int orc_ssa_ensemble(int lx, int ly, int model, const double *rates6, double T,
  * set into lat. events[i] receives cell cells[i]'s event count and amb[i]
  * its ambiguity flag. Returns 0, or -1 on invalid arguments. */
 int orc_window_cells(int lx, int ly, int qx, int qy, int model,
-                     const double *rates6, int col, double h, uint32_t w,
+                     const double *rates7, int col, double h, uint32_t w,
                      uint64_t seed, uint32_t rep, uint8_t *lat, int ncells,
                      const int32_t *cells, int32_t *events, int32_t *amb)
 {
     sys_t S;
-    if (qx < 1 || qy < 1 || lx % (2 * qx) || ly % (2 * qy)) return -1;
-    if (sys_init(&S, lx, ly, qx, qy, model, rates6)) return -1;
+    if (!geometry_ok(model, lx, ly, qx, qy)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
     for (int i = 0; i < ncells; i++) {
         int m = cells[i];
         if (m < 0 || m >= S.ncx * S.ncy) return -1;
