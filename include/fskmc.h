@@ -63,7 +63,13 @@ typedef enum {
     /* ZGB CO-oxidation (Table COrates): A adsorbs (yA), B2 adsorbs on an
        empty pair ((1-yA)/4 per directed pair), A+B react ((kr/4) per
        directed pair), A desorbs (kd) */
-    FSKMC_ZGB = 3
+    FSKMC_ZGB = 3,
+    /* 1D Ising benchmark of Section 7 (Eq. exactcov1d): a ring of lx sites
+       (ly = 1, cells qx x 1, neighbours x-1 and x+1 only) with
+       H = -K sum s(x) s(x+1) + h sum s(x), betaJ = beta K and betah = beta h:
+       r(0) = ka, r(1, n) = kd exp(-(betaJ n - betah)), n = occupied
+       neighbours (0..2); detailed-balanced with H when ka = kd */
+    FSKMC_ISING1D = 4
 } fskmc_model;
 
 /* Processor communication schedules (Section 3). */
@@ -89,7 +95,8 @@ typedef enum { FSKMC_CLOCK_FP64 = 0, FSKMC_CLOCK_FP32 = 1 } fskmc_clock;
 typedef enum { FSKMC_ENGINE_PLAIN = 0, FSKMC_ENGINE_PERSISTENT = 1 } fskmc_engine;
 
 typedef struct {
-    int32_t lx, ly;    /* lattice sides; lx % (2 qx) == 0 and ly % (2 qy) == 0 */
+    int32_t lx, ly;    /* lattice sides; lx % (2 qx) == 0 and ly % (2 qy) == 0
+                          (ISING1D: ly == 1, a ring of lx sites) */
     int32_t bitpacked; /* 1: keep the lattice in device memory at 1 bit per site (32 sites of a
                           row per 32-bit word); spin-flip models only, lx % 32 == 0. The ABI
                           still exchanges one byte per site. Results are identical. */
@@ -97,11 +104,13 @@ typedef struct {
 
 typedef struct {
     double ka, kd, betaJ, nu, yA, kr; /* fields a model does not use are ignored */
+    double betah;                     /* ISING1D: beta times the external field h */
 } fskmc_rates;
 
 typedef struct {
-    int32_t qx, qy; /* coarse cell shape, 1..32 each with qx*qy <= 1024;
-                       {0,0} asks the autotuner to pick a square q in {8,16,32} */
+    int32_t qx, qy; /* coarse cell shape, 1..32 each with qx*qy <= 1024 (ISING1D:
+                       qy = 1 and qx in 1..1024); {0,0} asks the autotuner to pick
+                       a square q in {8,16,32} (ISING1D: qx in {1024, 512, ..., 32}) */
 } fskmc_cell_shape;
 
 /*
@@ -221,11 +230,13 @@ fskmc_status fskmc_set_window_index(fskmc_ctx *ctx, uint64_t w);
 /*
  * Observables of Section 7 for one replica, from exact integer sums:
  * coverage[3] = fraction of sites in state 0, 1, 2; energy = -(occupied
- * nearest-neighbour pairs)/N for ADSDES and ADSDES_DIFFUSION,
+ * nearest-neighbour pairs)/N for ADSDES, ADSDES_DIFFUSION and ISING1D,
  * -(1/N) sum_<xy> s_x s_y with s = 2 sigma - 1 for ISING, NaN for ZGB;
  * paircorr[2*rmax] = G_x(1..rmax) then G_y(1..rmax), G_e(r) = (1/N) sum_x
  * [sigma(x)=1][sigma(x + r e)=1]. paircorr may be NULL when rmax == 0.
- * EINVAL: rmax < 0 or rmax > min(lx, ly), NULL coverage/energy.
+ * A lattice with ly == 1 is a ring: it has no vertical bonds, and its
+ * vertical pairs and G_y are 0.
+ * EINVAL: rmax < 0, rmax > lx, rmax > ly when ly > 1, NULL coverage/energy.
  */
 fskmc_status fskmc_observables(fskmc_ctx *ctx, int32_t replica, double *coverage,
                                double *energy, double *paircorr, int32_t rmax);
@@ -259,7 +270,8 @@ fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
 
 /*
  * Autotuner for the batched workload: for every square cell size q in
- * {8, 16, 32} that all n lattices admit and warps per block in {2, 4, 8},
+ * {8, 16, 32} (ISING1D: cells of q x 1 sites, q in {32, 64, ..., 1024})
+ * that all n lattices admit and warps per block in {2, 4, 8},
  * builds a scratch batch context (lattices[n], rates[n], model; Bernoulli
  * (coverage) start from seed), runs one warm-up step and times 4 steps of
  * `scheme` with window dt on the given engine and clock (CUDA events on
@@ -298,8 +310,8 @@ fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_mode
  * capture. The call allocates neither device nor host heap memory.
  *
  * EINVAL: NULL lattice/coverage/energy (or paircorr with rmax > 0), unknown
- * model, lx or ly < 1, lx*ly > 2^31, rmax < 0, rmax > min(lx, ly) or
- * rmax > FSKMC_NOALLOC_MAX_RMAX. ECUDA: a CUDA call failed.
+ * model, lx or ly < 1, lx*ly > 2^31, rmax < 0, rmax > lx, rmax > ly when
+ * ly > 1, or rmax > FSKMC_NOALLOC_MAX_RMAX. ECUDA: a CUDA call failed.
  */
 #define FSKMC_NOALLOC_MAX_RMAX 256
 fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_t lx, int32_t ly,

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfskmc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 MODELS = {"ADSDES": 0, "ISING": 1, "ISING_ARRHENIUS": 1, "DIFFUSION": 2, "ADSDES_DIFFUSION": 2,
-          "ZGB": 3}
+          "ZGB": 3, "ISING1D": 4}
 SCHEMES = {"LIE": 0, "STRANG": 1, "RANDOM": 2, "RANDOM_ORDER": 3}
 CLOCKS = {"FP64": 0, "FP32": 1}
 ENGINES = {"PLAIN": 0, "PERSISTENT": 1}
@@ -52,7 +52,8 @@ class Lattice(C.Structure):
 
 class Rates(C.Structure):
     _fields_ = [("ka", C.c_double), ("kd", C.c_double), ("betaJ", C.c_double),
-                ("nu", C.c_double), ("yA", C.c_double), ("kr", C.c_double)]
+                ("nu", C.c_double), ("yA", C.c_double), ("kr", C.c_double),
+                ("betah", C.c_double)]
 
 
 class CellShape(C.Structure):
@@ -125,7 +126,7 @@ def _check(status: int, ctx=None):
 
 def _rates(d: dict) -> Rates:
     return Rates(d.get("ka", 1.0), d.get("kd", 1.0), d.get("betaJ", 0.0), d.get("nu", 0.0),
-                 d.get("yA", 0.0), d.get("kr", 0.0))
+                 d.get("yA", 0.0), d.get("kr", 0.0), d.get("betah", 0.0))
 
 
 def _stream_ptr(stream):

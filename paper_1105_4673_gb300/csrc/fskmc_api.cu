@@ -101,6 +101,12 @@ int class_rates(int model, const fskmc_rates &q, double *r)
         r[2] = q.kr * 0.25;
         r[3] = q.kd;
         return 4;
+    case fskmc::ISING1D:
+        for (int n = 0; n < 3; ++n) {
+            r[n] = q.ka;
+            r[3 + n] = q.kd * std::exp(-(q.betaJ * (double)n - q.betah));
+        }
+        return 6;
     }
     return -1;
 }
@@ -122,6 +128,12 @@ fskmc_status check_rates(int model, const fskmc_rates &q)
         if (!(q.yA >= 0.0 && q.yA <= 1.0) || !finite_nonneg(q.kr) || !finite_nonneg(q.kd))
             return fail(nullptr, FSKMC_EINVAL, "rates: yA must be in [0,1], kr and kd finite and >= 0");
         break;
+    case fskmc::ISING1D:
+        if (!finite_nonneg(q.ka) || !finite_nonneg(q.kd) || !std::isfinite(q.betaJ) ||
+            !std::isfinite(q.betah))
+            return fail(nullptr, FSKMC_EINVAL,
+                        "rates: ka, kd must be finite and >= 0, betaJ and betah finite");
+        break;
     default:
         return fail(nullptr, FSKMC_EINVAL, "unknown model %d", model);
     }
@@ -136,10 +148,22 @@ fskmc_status check_rates(int model, const fskmc_rates &q)
 fskmc_status check_geometry(int model, const fskmc_lattice &L, int qx, int qy)
 {
     if (L.bitpacked != 0 && L.bitpacked != 1) return fail(nullptr, FSKMC_EINVAL, "bitpacked must be 0 or 1");
-    if (L.bitpacked && model != fskmc::ADSDES && model != fskmc::ISING)
+    if (L.bitpacked && model != fskmc::ADSDES && model != fskmc::ISING && model != fskmc::ISING1D)
         return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices are for the spin-flip models");
     if (L.bitpacked && L.lx % 32)
         return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices need lx to be a multiple of 32");
+    if (model == fskmc::ISING1D) {
+        // a ring of lx sites: one row of cells qx x 1
+        if (L.ly != 1 || qy != 1)
+            return fail(nullptr, FSKMC_EINVAL, "ISING1D is a ring: ly and qy must be 1");
+        if (qx < 1 || qx > fskmc::MAX_Q_RING)
+            return fail(nullptr, FSKMC_EINVAL, "ring cell length %d out of range 1..%d", qx,
+                        fskmc::MAX_Q_RING);
+        if (L.lx < 2 * qx || L.lx % (2 * qx))
+            return fail(nullptr, FSKMC_EINVAL, "ring of %d sites is not a positive multiple of 2*%d",
+                        L.lx, qx);
+        return FSKMC_OK;
+    }
     if (qx < 1 || qy < 1 || qx > fskmc::MAX_Q || qy > fskmc::MAX_Q)
         return fail(nullptr, FSKMC_EINVAL, "cell shape %dx%d out of range 1..32", qx, qy);
     if (L.lx < 2 * qx || L.ly < 2 * qy || L.lx % (2 * qx) || L.ly % (2 * qy))
@@ -233,10 +257,29 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
 {
     if (!out || !lats || !rates) return fail(nullptr, FSKMC_EINVAL, "NULL argument");
     *out = nullptr;
-    if ((int)model < 0 || (int)model > 3) return fail(nullptr, FSKMC_EINVAL, "unknown model %d", (int)model);
+    if ((int)model < 0 || (int)model > 4) return fail(nullptr, FSKMC_EINVAL, "unknown model %d", (int)model);
     if (n < 1 || n > 65536) return fail(nullptr, FSKMC_EINVAL, "replica count %d out of range", n);
     int qx = cell.qx, qy = cell.qy;
-    if (qx == 0 && qy == 0) {
+    if (qx == 0 && qy == 0 && (int)model == fskmc::ISING1D) {
+        // Ring: the longest cell in {1024, ..., 32} that every ring admits
+        // and that leaves at least 152 active cells in total, else the
+        // longest admissible one.
+        int best = 0;
+        for (int q = fskmc::MAX_Q_RING; q >= 32; q >>= 1) {
+            bool ok = true;
+            int64_t cells = 0;
+            for (int r = 0; r < n && ok; ++r) {
+                ok = lats[r].ly == 1 && lats[r].lx >= 2 * q && lats[r].lx % (2 * q) == 0;
+                cells += ok ? lats[r].lx / q / 2 : 0;
+            }
+            if (!ok) continue;
+            if (!best) best = q;
+            if (cells >= 152) { best = q; break; }
+        }
+        if (!best) return fail(nullptr, FSKMC_EINVAL, "no ring cell length in {32..1024} fits every ring");
+        qx = best;
+        qy = 1;
+    } else if (qx == 0 && qy == 0) {
         // Autotuner: the largest square cell in {32, 16, 8} that every
         // replica admits and that leaves at least 152 active cells in total
         // (one per SM); falling back to the largest admissible one.
@@ -286,7 +329,8 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
         R.cell_off = coff;
         R.rep = (uint32_t)r;
         c->nclass = class_rates(model, rates[r], R.r);
-        set_fixed_point(R, c->nclass, qx * qy * ((int)model >= fskmc::DIFFUSION ? 9 : 1));
+        const bool two_site = (int)model == fskmc::DIFFUSION || (int)model == fskmc::ZGB;
+        set_fixed_point(R, c->nclass, qx * qy * (two_site ? 9 : 1));
         const int64_t bytes = c->packed ? (int64_t)(R.lx / 32) * R.ly * 4 : (int64_t)R.lx * R.ly;
         off += (bytes + 255) & ~(int64_t)255;
         coff += R.ncx * R.ncy;
@@ -658,7 +702,8 @@ fskmc_status fskmc_observables(fskmc_ctx *c, int32_t replica, double *coverage, 
     if (!c) return FSKMC_EINVAL;
     if (replica < 0 || replica >= c->nrep) return fail(c, FSKMC_EINVAL, "bad replica %d", replica);
     const Replica &R = c->reps[replica];
-    if (!coverage || !energy || rmax < 0 || rmax > R.lx || rmax > R.ly || (rmax > 0 && !paircorr))
+    if (!coverage || !energy || rmax < 0 || rmax > R.lx || (R.ly > 1 && rmax > R.ly) ||
+        (rmax > 0 && !paircorr))
         return fail(c, FSKMC_EINVAL, "bad observables arguments");
     int need = 4 + 2 * rmax;
     if (need > c->obs_cap) {
@@ -775,9 +820,16 @@ fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_mode
     double best = -1.0;
     fskmc_cell_shape bc = {0, 0};
     int bw = 0;
-    for (int q : {8, 16, 32}) {
+    // square cells in {8, 16, 32}; on a ring, cells of 32..1024 sites
+    std::vector<fskmc_cell_shape> shapes;
+    if ((int)model == fskmc::ISING1D) {
+        for (int q = 32; q <= fskmc::MAX_Q_RING; q <<= 1) shapes.push_back({q, 1});
+    } else {
+        for (int q : {8, 16, 32}) shapes.push_back({q, q});
+    }
+    for (const fskmc_cell_shape &shape : shapes) {
         fskmc_ctx *c = nullptr;
-        if (make_ctx(n, lattices, model, rates, fskmc_cell_shape{q, q}, stream, true, &c) != FSKMC_OK)
+        if (make_ctx(n, lattices, model, rates, shape, stream, true, &c) != FSKMC_OK)
             continue;  // this cell size does not fit every lattice
         fskmc_status st = fskmc_set_clock(c, clock);
         if (!st) st = fskmc_set_engine(c, engine);
@@ -804,14 +856,14 @@ fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_mode
             const double rate = ms > 0.0f ? (double)(after[0] - before[0]) / (ms * 1e-3) : 0.0;
             if (rate > best) {
                 best = rate;
-                bc = fskmc_cell_shape{q, q};
+                bc = shape;
                 bw = wpb;
             }
         }
         fskmc_destroy(c);
-        if (st) return fail(nullptr, st, "autotune trial failed for q=%d", q);
+        if (st) return fail(nullptr, st, "autotune trial failed for cell %dx%d", shape.qx, shape.qy);
     }
-    if (best < 0.0) return fail(nullptr, FSKMC_EINVAL, "no cell size in {8,16,32} fits every lattice");
+    if (best < 0.0) return fail(nullptr, FSKMC_EINVAL, "no candidate cell shape fits every lattice");
     *best_cell = bc;
     *best_wpb = bw;
     if (best_rate) *best_rate = best;

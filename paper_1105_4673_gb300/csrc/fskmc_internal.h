@@ -5,10 +5,11 @@
 
 namespace fskmc {
 
-enum Model : int { ADSDES = 0, ISING = 1, DIFFUSION = 2, ZGB = 3 };
+enum Model : int { ADSDES = 0, ISING = 1, DIFFUSION = 2, ZGB = 3, ISING1D = 4 };
 
 constexpr int MAX_CLASSES = 16;
 constexpr int MAX_Q = 32;
+constexpr int MAX_Q_RING = 1024;  // cell length on a ring (ISING1D)
 constexpr int MAX_CELL_SITES = 1024;
 
 // Per-replica description, resident on the device.

@@ -76,8 +76,12 @@ __device__ __forceinline__ int site_at(const uint8_t *lat, int lx, int y, int x)
     return lat[(int64_t)y * lx + x];
 }
 
-// One block per row (grid-stride over rows). Accumulators in shared memory
-// as 32-bit per block, flushed with 64-bit atomics.
+// Row chunks of OBS_CHUNK sites, one per block (grid-stride over the rows'
+// chunks). Accumulators in shared memory as 32-bit per block, flushed with
+// 64-bit atomics. A ring (ly == 1) has no vertical bonds: its vertical pairs
+// and G_y are 0.
+constexpr int OBS_CHUNK = 4096;
+
 template <bool PACKED>
 __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
                                    unsigned long long *out)
@@ -87,18 +91,23 @@ __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
     for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    for (int y = blockIdx.x; y < ly; y += gridDim.x) {
+    const bool vert = ly > 1;
+    const int nch = (lx + OBS_CHUNK - 1) / OBS_CHUNK;
+    for (int64_t task = blockIdx.x; task < (int64_t)ly * nch; task += gridDim.x) {
+        const int y = (int)(task / nch);
+        const int xa = (int)(task % nch) * OBS_CHUNK;
+        const int xb = min(lx, xa + OBS_CHUNK);
         const int yd = (y + 1) % ly;
-        // counts and nearest-neighbour pairs; lx is a multiple of 32 or the
-        // tail is handled by the predicate, so every lane reaches the reduces
-        for (int x0 = 0; x0 < lx; x0 += blockDim.x) {
+        // counts and nearest-neighbour pairs; the tail is handled by the
+        // predicate, so every lane reaches the reduces
+        for (int x0 = xa; x0 < xb; x0 += blockDim.x) {
             int x = x0 + threadIdx.x;
             unsigned int c0 = 0, c1 = 0, c2 = 0, pr = 0;
-            const int s = x < lx ? site_at<PACKED>(lat, lx, y, x) : -1;
-            if (x < lx) {
+            const int s = x < xb ? site_at<PACKED>(lat, lx, y, x) : -1;
+            if (x < xb) {
                 c0 = s == 0; c1 = s == 1; c2 = s == 2;
                 if (s == 1) pr = (site_at<PACKED>(lat, lx, y, (x + 1) % lx) == 1) +
-                                 (site_at<PACKED>(lat, lx, yd, x) == 1);
+                                 (vert && site_at<PACKED>(lat, lx, yd, x) == 1);
             }
             c0 = __reduce_add_sync(0xffffffffu, c0);
             c1 = __reduce_add_sync(0xffffffffu, c1);
@@ -112,7 +121,7 @@ __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
                 unsigned int gxv = 0, gyv = 0;
                 if (s == 1) {
                     gxv = site_at<PACKED>(lat, lx, y, (x + r) % lx) == 1;
-                    gyv = site_at<PACKED>(lat, lx, (y + r) % ly, x) == 1;
+                    gyv = vert && site_at<PACKED>(lat, lx, (y + r) % ly, x) == 1;
                 }
                 gxv = __reduce_add_sync(0xffffffffu, gxv);
                 gyv = __reduce_add_sync(0xffffffffu, gyv);
@@ -165,7 +174,8 @@ cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned
 cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
                                unsigned long long *out, cudaStream_t s, bool packed)
 {
-    int grid = ly < 152 * 8 ? ly : 152 * 8;
+    const int64_t tasks = (int64_t)ly * ((lx + OBS_CHUNK - 1) / OBS_CHUNK);
+    const int grid = tasks < 152 * 8 ? (int)tasks : 152 * 8;
     size_t smem = sizeof(unsigned int) * (size_t)(4 + 2 * rmax);
     if (packed) observables_kernel<true><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
     else observables_kernel<false><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);

@@ -58,9 +58,10 @@ extern "C" fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_
                                                   double *paircorr, int32_t rmax)
 {
     if (!lattice || !coverage || !energy) return FSKMC_EINVAL;
-    if ((int)model < 0 || (int)model > 3) return FSKMC_EINVAL;
+    if ((int)model < 0 || (int)model > 4) return FSKMC_EINVAL;
     if (lx < 1 || ly < 1 || (int64_t)lx * ly > ((int64_t)1 << 31)) return FSKMC_EINVAL;
-    if (rmax < 0 || rmax > FSKMC_NOALLOC_MAX_RMAX || rmax > lx || rmax > ly) return FSKMC_EINVAL;
+    if (rmax < 0 || rmax > FSKMC_NOALLOC_MAX_RMAX || rmax > lx || (ly > 1 && rmax > ly))
+        return FSKMC_EINVAL;
     if (rmax > 0 && !paircorr) return FSKMC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     void *scratch = nullptr;

@@ -43,6 +43,11 @@ template <> struct Traits<ADSDES> { static constexpr int K = 10, KS = 10, KB = 0
 template <> struct Traits<ISING> { static constexpr int K = 10, KS = 10, KB = 0, HW = 1, R = 1; };
 template <> struct Traits<DIFFUSION> { static constexpr int K = 15, KS = 10, KB = 5, HW = 2, R = 2; };
 template <> struct Traits<ZGB> { static constexpr int K = 4, KS = 2, KB = 2, HW = 1, R = 1; };
+template <> struct Traits<ISING1D> { static constexpr int K = 6, KS = 6, KB = 0, HW = 1, R = 1; };
+
+// Spin-flip models: class = SPIN_STRIDE * sigma + n, n = occupied neighbours.
+template <int MODEL>
+constexpr bool is_spin_flip() { return MODEL == ADSDES || MODEL == ISING || MODEL == ISING1D; }
 
 __device__ __forceinline__ int dir_dx(int d) { return d == 1 ? 1 : (d == 3 ? -1 : 0); }
 __device__ __forceinline__ int dir_dy(int d) { return d == 0 ? -1 : (d == 2 ? 1 : 0); }
@@ -80,6 +85,7 @@ __device__ __forceinline__ int site_class(const uint8_t *box, int BW, int p)
 {
     int s = box[p];
     if (MODEL == ZGB) return s == 0 ? 0 : (s == 1 ? 3 : -1);
+    if (MODEL == ISING1D) return 3 * s + (box[p - 1] == 1) + (box[p + 1] == 1);  // ring: x -+ 1
     return 5 * s + occ4<MODEL>(box, BW, p);
 }
 
@@ -362,18 +368,22 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             if (lane == 2) box[by * BW + BW - 1] = ld_site<PERSIST>(srow + (X0 + 32 == lx ? 0 : X0 + 32));
         }
     } else {
-        // Stage the cell and its halo (periodic wrap) from the window-start state.
-        for (int i = lane; i < BW * BH; i += 32) {
-            int by = i / BW, bx = i - by * BW;
+        // Stage the cell and its halo (periodic wrap) from the window-start
+        // state; on the ring only the cell's own row (the rows above and
+        // below are never read).
+        constexpr bool ring = MODEL == ISING1D;
+        for (int i = lane; i < (ring ? BW : BW * BH); i += 32) {
+            int by = ring ? HW : i / BW, bx = ring ? i : i - by * BW;
             int gy = Y0 - HW + by, gx = X0 - HW + bx;
             gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
             gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+            const int bi = by * BW + bx;
             if (PACKED) {
                 const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
                 const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
-                box[i] = (uint8_t)((wv >> (gx & 31)) & 1u);
+                box[bi] = (uint8_t)((wv >> (gx & 31)) & 1u);
             } else {
-                box[i] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+                box[bi] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
             }
         }
     }
@@ -672,19 +682,23 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             else { ox += dir_dx(dir); oy += dir_dy(dir); }
         }
         const int po = (oy + HW) * BW + ox + HW, pt = (ty + HW) * BW + tx + HW;
-        if (MODEL == ADSDES || MODEL == ISING) {
-            // Spin flip at (sx, sy): its class k = 5 sigma + n becomes k -+ 5,
+        if (is_spin_flip<MODEL>()) {
+            // Spin flip at (sx, sy): its class k = S sigma + n becomes k -+ S,
             // and each neighbour inside the cell changes n by +-1. The new
             // classes follow from the old ones; no lattice reads needed.
-            const int sold = k >= 5;
+            // S = 5 with neighbours N, E, S, W (lanes 1..4); on the ring
+            // S = 3 with neighbours E, W (lanes 1, 2).
+            constexpr int SK = MODEL == ISING1D ? 3 : 5;
+            const int sold = k >= SK;
             if (lane == 0) box[po] = (uint8_t)(1 - sold);
-            if (lane < 5) {
+            if (lane < SK) {
                 int ux = sx, uy = sy;
-                if (lane > 0) { ux += dir_dx(lane - 1); uy += dir_dy(lane - 1); }
+                if (MODEL == ISING1D) { ux += lane == 1 ? 1 : (lane == 2 ? -1 : 0); }
+                else if (lane > 0) { ux += dir_dx(lane - 1); uy += dir_dy(lane - 1); }
                 if (ux >= 0 && ux < qx && uy >= 0 && uy < qy) {
                     const int i = uy * qx + ux;
                     int kold, knew;
-                    if (lane == 0) { kold = k; knew = sold ? k - 5 : k + 5; }
+                    if (lane == 0) { kold = k; knew = sold ? k - SK : k + SK; }
                     else { kold = (int8_t)scls[i]; knew = kold + (sold ? -1 : 1); }
                     scls[i] = (uint8_t)knew;
                     const int own = i >> 5;
@@ -698,7 +712,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         } else {
             // Apply the event (the update sigma -> sigma^{x,omega}).
             if (lane == 0) {
-                if (MODEL == ADSDES || MODEL == ISING) {
+                if (is_spin_flip<MODEL>()) {
                     box[po] ^= 1;
                 } else if (MODEL == DIFFUSION) {
                     if (k < 10) box[po] ^= 1;
@@ -783,27 +797,27 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     // Write back the write set: own sites, plus the halo ends of owned cross
     // bonds for the two-site models (columns in E windows, rows in O windows).
     if (PACKED) {
-        // one row per lane; a word shared with other cells (cells narrower
-        // than 32 sites) is updated with atomics on this cell's bits only
+        // one (row, word) pair per lane; a word shared with other cells
+        // (cells narrower than 32 sites) is updated with atomics on this
+        // cell's bits only
         uint32_t *dst32 = reinterpret_cast<uint32_t *>(dst);
-        for (int row = lane; row < qy; row += 32) {
+        const int wa = X0 >> 5, nwr = ((X0 + qx - 1) >> 5) - wa + 1;
+        for (int t = lane; t < qy * nwr; t += 32) {
+            const int row = t / nwr, wi = wa + (t - row * nwr);
             const uint8_t *brow = box + (row + HW) * BW + HW - X0;
             uint32_t *drow = dst32 + (int64_t)(Y0 + row) * (lx >> 5);
-            for (int x = X0; x < X0 + qx;) {
-                const int wi = x >> 5, xe = min(X0 + qx, (wi + 1) << 5);
-                uint32_t mask = 0u, bits = 0u;
-                for (int xx = x; xx < xe; ++xx) {
-                    const uint32_t b = 1u << (xx & 31);
-                    mask |= b;
-                    if (brow[xx]) bits |= b;
-                }
-                if (mask == 0xffffffffu) {
-                    drow[wi] = bits;
-                } else {
-                    atomicAnd(drow + wi, ~mask);
-                    atomicOr(drow + wi, bits);
-                }
-                x = xe;
+            const int xs = max(X0, wi << 5), xe = min(X0 + qx, (wi + 1) << 5);
+            uint32_t mask = 0u, bits = 0u;
+            for (int xx = xs; xx < xe; ++xx) {
+                const uint32_t b = 1u << (xx & 31);
+                mask |= b;
+                if (brow[xx]) bits |= b;
+            }
+            if (mask == 0xffffffffu) {
+                drow[wi] = bits;
+            } else {
+                atomicAnd(drow + wi, ~mask);
+                atomicOr(drow + wi, bits);
             }
         }
     } else {
@@ -992,12 +1006,14 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
             // epoch[c] = 1 + the last window in which cell c was active.
             // Lane 0: this cell's previous active window; lanes 1..4: the
             // edge neighbours' last active window before this one.
+            // A ring (one row of cells) has no vertical neighbours.
             const int2 pv = P.prev[widx];
             const int ex = lane == 1 ? 1 : (lane == 3 ? -1 : 0);
             const int ey = lane == 2 ? 1 : (lane == 4 ? -1 : 0);
             const int dcx = (cx + ex + R.ncx) % R.ncx, dcy = (cy + ey + R.ncy) % R.ncy;
             const int target = (lane == 0 ? pv.x : pv.y) + 1;
-            ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 5 && target > 0, target, P, lane);
+            const bool dep = lane < 5 && target > 0 && !(ey != 0 && R.ncy == 1);
+            ok = wait_epochs(ep, dcy * R.ncx + dcx, dep, target, P, lane);
         } else {
             // ping-pong: every cell has a task in every window and
             // epoch[c] = 1 + the last window whose reads and writes of cell
@@ -1045,7 +1061,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     int blocks = (nactive + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
     void (*kern)(WindowArgs, int, int) = nullptr;
-    if constexpr (MODEL == ADSDES || MODEL == ISING) {
+    if constexpr (is_spin_flip<MODEL>()) {
         if (a.packed) kern = fp32 ? fs_window_kernel<MODEL, float, true> : fs_window_kernel<MODEL, double, true>;
     }
     if (!kern) kern = fp32 ? fs_window_kernel<MODEL, float, false> : fs_window_kernel<MODEL, double, false>;
@@ -1057,7 +1073,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
 template <int MODEL>
 void *persistent_kernel_ptr(int fp32, bool packed)
 {
-    if constexpr (MODEL == ADSDES || MODEL == ISING) {
+    if constexpr (is_spin_flip<MODEL>()) {
         if (packed)
             return fp32 ? (void *)fs_persistent_kernel<MODEL, float, true>
                         : (void *)fs_persistent_kernel<MODEL, double, true>;
@@ -1073,6 +1089,7 @@ void *persistent_kernel_for(int model, int fp32, bool packed)
     case ISING: return persistent_kernel_ptr<ISING>(fp32, packed);
     case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false);
     case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false);
+    case ISING1D: return persistent_kernel_ptr<ISING1D>(fp32, packed);
     }
     return nullptr;
 }
@@ -1086,6 +1103,7 @@ size_t window_smem_per_warp(int model, int qx, int qy)
     case ISING: return make_layout<ISING>(qx, qy).bytes;
     case DIFFUSION: return make_layout<DIFFUSION>(qx, qy).bytes;
     case ZGB: return make_layout<ZGB>(qx, qy).bytes;
+    case ISING1D: return make_layout<ISING1D>(qx, qy).bytes;
     }
     return 0;
 }
@@ -1098,6 +1116,7 @@ cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int nactive,
     case ISING: return launch_model<ISING>(fp32, a, nactive, wpb, st);
     case DIFFUSION: return launch_model<DIFFUSION>(fp32, a, nactive, wpb, st);
     case ZGB: return launch_model<ZGB>(fp32, a, nactive, wpb, st);
+    case ISING1D: return launch_model<ISING1D>(fp32, a, nactive, wpb, st);
     }
     return cudaErrorInvalidValue;
 }

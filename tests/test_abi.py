@@ -55,6 +55,12 @@ def _create(lib, lx, ly, model, q, rates=None):
     (64, 64, 3, (8, 8), dict(yA=1.5)),  # yA outside [0,1]
     (64, 64, 7, (8, 8), {}),            # unknown model
     (64, 64, 1, (8, 8), dict(betaJ=float("nan"))),
+    (64, 2, 4, (8, 1), {}),             # ring: ly must be 1
+    (64, 1, 4, (8, 2), {}),             # ring: qy must be 1
+    (96, 1, 4, (64, 1), {}),            # ring of 96 not a multiple of 128
+    (4096, 1, 4, (2048, 1), {}),        # ring cell longer than 1024
+    (64, 1, 4, (8, 1), dict(betah=float("inf"))),
+    (64, 1, 0, (8, 1), {}),             # a 2D model on one row
 ])
 def test_create_rejects_invalid_arguments(lib, lx, ly, model, q, rates):
     st, h = _create(lib, lx, ly, model, q, rates)
@@ -85,7 +91,8 @@ def test_schedule_matches_oracle(lib, scheme, replica, w0):
 
 @pytest.mark.parametrize("lx,ly,model,q", [(64, 64, 3, (8, 8)),    # ZGB has three states
                                            (48, 48, 1, (8, 8)),    # lx not a multiple of 32
-                                           (64, 64, 2, (8, 8))])   # diffusion: not a spin flip
+                                           (64, 64, 2, (8, 8)),    # diffusion: not a spin flip
+                                           (48, 1, 4, (8, 1))])    # ring of 48 sites
 def test_bitpacked_validation(lib, lx, ly, model, q):
     h = C.c_void_p()
     st = lib.fskmc_create(C.byref(F.Lattice(lx, ly, 1)), model, C.byref(F._rates({})),
