@@ -125,11 +125,20 @@ FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
 # 152 SMs x 4 schedulers x 2.07 GHz.
 ISSUE_PEAK_G = 152 * 4 * 2.07
 
-# DRAM traffic per launch of fs_window_kernel<ISING,double> on this workload
-# from one ncu capture (profiles/fs_window_kernel_ising1024.md), valid only
-# for the kernel source it was taken on.
-PROFILED_TRAFFIC = {"src_sha256": "491f2df9b98e269b240e78d3bb53ff9711d1a50547052bc0860fc43176abb224",
-                    "bytes_per_launch": 1087744}
+# DRAM traffic per launch of fs_window_kernel<ISING,double> (bit-packed
+# lattice) on this workload from one ncu capture
+# (profiles/fs_window_kernel_ising1024.md), valid only for the kernel source
+# it was taken on.
+PROFILED_TRAFFIC = {"src_sha256": "44964402c1044a6be28afbe38e47d517409eaaa898cf06d73d2d5a8349d8a5d5",
+                    "bytes_per_launch": 170240}
+
+
+def stage_bytes_per_site(w):
+    """Algorithmic bytes one window moves per active site: the cell and its
+    one-site halo read, the cell written, (1 + 2/q)^2 + 1 sites, at one byte
+    per site or one bit per site when bit-packed."""
+    q = w["q"][0]
+    return ((1.0 + 2.0 / q) ** 2 + 1.0) / (8.0 if w.get("bitpacked") else 1.0)
 
 
 def window_src_sha():
@@ -325,7 +334,8 @@ def main():
                      "algorithmic_ops_per_event": ops_per_event,
                      "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
                                    if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz") +
-                                  "; HBM is not the bound (2.27 B/site/window)"},
+                                  f"; HBM is not the bound ({stage_bytes_per_site(w):.2f} B per "
+                                  "active site per window)"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
                 "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
