@@ -26,7 +26,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import WORKLOADS  # noqa: E402
+from workloads import WORKLOADS, sample_shape  # noqa: E402
 
 METRIC = "KMC events/sec on 1 GB300 (batched FP32-clock vs plain FP64) at stated Δt-error"
 STEP_WINDOWS_DT = 10  # one bench step advances the lattice by 10 dt of physical time
@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--engine", default="plain", choices=["plain", "persistent"])
     p.add_argument("--clock", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--wpb", type=int, default=0, help="warps per CTA (0: the library default)")
+    p.add_argument("--order", default="auto", choices=["auto", "natural", "workload"],
+                   help="issue order of a window's active cells")
     return p.parse_args()
 
 
@@ -116,7 +119,7 @@ class ClockSampler:
 # warp-uniform instruction of the cell's warp: the ordered fused
 # multiply-add chain over the model's K classes, the divide, the threshold
 # multiply, the clock add and the logarithm.
-NCLASSES = {"ADSDES": 10, "ISING": 10, "DIFFUSION": 15, "ZGB": 4}
+NCLASSES = {"ADSDES": 10, "ISING": 10, "DIFFUSION": 15, "ZGB": 4, "ISING1D": 6}
 # Peak: the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp instructions,
 # 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
 FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
@@ -131,6 +134,15 @@ ISSUE_PEAK_G = 152 * 4 * 2.07
 # it was taken on.
 PROFILED_TRAFFIC = {"src_sha256": "44964402c1044a6be28afbe38e47d517409eaaa898cf06d73d2d5a8349d8a5d5",
                     "bytes_per_launch": 170240}
+
+
+def init_state(ctx, w, seed):
+    """The workload's initial state: the seeded Gaussian bump of species A on
+    an empty lattice where the workload names one, else Bernoulli coverage."""
+    if "bump" in w:
+        ctx.init_bump(seed, w["bump"]["amp"], w["bump"]["width"], 1)
+    else:
+        ctx.init_random(seed, w.get("coverage", 0.5))
 
 
 def stage_bytes_per_site(w):
@@ -149,11 +161,12 @@ def window_src_sha():
 
 def cpu_baseline(w, seconds):
     """The oracle as it stands on a bounded sample of the workload: a 256x256
-    lattice of the same model, rates, cell shape and schedule, advanced step
-    by step until `seconds` of CPU time. Events/s do not depend on the
-    lattice size for the cell-by-cell oracle (cost per event ~ cell size)."""
+    lattice (a ring of 8192 sites for the 1D model) of the same model, rates,
+    cell shape and schedule, advanced step by step until `seconds` of CPU
+    time. Events/s do not depend on the lattice size for the cell-by-cell
+    oracle (cost per event ~ cell size)."""
     import oracle
-    lx = ly = 256
+    lx, ly = sample_shape(w)
     run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
                        oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
     t0 = time.process_time()
@@ -163,7 +176,7 @@ def cpu_baseline(w, seconds):
         steps += 1
     dt = max(time.process_time() - t0, 1e-9)
     return {"value": run.events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"256x256 lattice, same model/rates/cells/schedule, {steps} Lie steps "
+            "sample": f"{lx}x{ly} lattice, same model/rates/cells/schedule, {steps} steps "
                       f"of dt={w['dt']} ({run.events} events, {dt:.1f} s CPU, single thread)"}
 
 
@@ -174,7 +187,7 @@ def run_reference(args, rank, world):
     cb = None
     vals = []
     import oracle
-    lx = ly = 256
+    lx, ly = sample_shape(w)
     run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
                        oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
     for i in range(args.warmup + args.steps):
@@ -188,14 +201,14 @@ def run_reference(args, rank, world):
     tt = sum(v[1] for v in vals)
     value = ev / tt
     cb = {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
-          "sample": f"256x256 lattice of the {args.workload} workload, one Lie step of dt="
+          "sample": f"{lx}x{ly} lattice of the {args.workload} workload, one step of dt="
                     f"{w['dt']} per bench step, single thread"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tt / max(len(vals), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload + " (256x256 sample on the host CPU)"},
+        "config": {"workload": args.workload + f" ({lx}x{ly} sample on the host CPU)"},
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
@@ -222,7 +235,10 @@ def main():
                     bitpacked=w.get("bitpacked", False))
     ctx.set_engine(args.engine.upper())
     ctx.set_clock(args.clock.upper())
-    ctx.init_random(seed, w.get("coverage", 0.5))
+    if args.wpb:
+        ctx.set_warps_per_block(args.wpb)
+    ctx.set_task_order(args.order.upper())
+    init_state(ctx, w, seed)
     step_t = STEP_WINDOWS_DT * w["dt"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -323,6 +339,7 @@ def main():
                    "step": f"{step_t:g} time units ({kernel_windows_per_step(F, w, step_t)} windows) "
                            "+ observables",
                    "clock": args.clock, "engine": args.engine,
+                   "warps_per_cta": ctx.info()["warps_per_block"], "task_order": args.order,
                    "storage": "1 bit/site" if w.get("bitpacked") else "1 byte/site",
                    "l2": "flushed between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
@@ -362,7 +379,7 @@ def measure_variants(F, w, stream, seed, steps):
                       bitpacked=w.get("bitpacked", False))
         c.set_engine(engine)
         c.set_clock(clock)
-        c.init_random(seed, w.get("coverage", 0.5))
+        init_state(c, w, seed)
         step_t = STEP_WINDOWS_DT * w["dt"]
         c.run(w["scheme"], w["dt"], step_t, seed)
         torch.cuda.synchronize()
@@ -416,7 +433,8 @@ def clock_error(F, stream, w, n=64, L=128, T=10.0):
     replicas of an L x L lattice of the workload's model (mean difference and
     its standard error), and each form's dt-error estimate against dt/16."""
     import torch
-    reps = [dict(lx=L, ly=L, rates=w["rates"]) for _ in range(n)]
+    shape = (L * L, 1) if w["model"] == "ISING1D" else (L, L)
+    reps = [dict(lx=shape[0], ly=shape[1], rates=w["rates"]) for _ in range(n)]
 
     def run(clock, dt, seed):
         b = F.Context(model=w["model"], q=w["q"], batch=reps, stream=stream)
@@ -432,7 +450,7 @@ def clock_error(F, stream, w, n=64, L=128, T=10.0):
         b.close()
         return obs
 
-    out = {"replicas": n, "lattice": f"{L}x{L}", "T": T, "dt": w["dt"]}
+    out = {"replicas": n, "lattice": f"{shape[0]}x{shape[1]}", "T": T, "dt": w["dt"]}
     f64 = run("FP64", w["dt"], 101)
     f32 = run("FP32", w["dt"], 202)
     ref = run("FP64", w["dt"] / 16, 303)

@@ -156,6 +156,28 @@ fskmc_status fskmc_set_engine(fskmc_ctx *ctx, fskmc_engine engine);
    Results do not depend on it. */
 fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
 
+/* Order in which the active cells of a window are issued (Section 6,
+   Eq. wload). The paper rebalances by reshaping the cells so that each
+   processor receives equal work; here the cells keep their shape and the
+   active cells of a window are handed to the GPU's block scheduler (plain
+   engine) or task queue (persistent engine) heaviest first, by their event
+   count W(m) in their previous window (longest-processing-time-first list
+   scheduling). NATURAL: row-major cell order. WORKLOAD: heaviest first,
+   from the counts each cell had when the fskmc_run or fskmc_window call
+   began. AUTO (default): WORKLOAD in the plain engine when a window's
+   active cells fill the GPU in one wave (8 to 16 per SM; the block scheduler
+   then spreads the heaviest cells over the SMs), else NATURAL (with several
+   waves the scheduler balances by itself and row-major order keeps
+   neighbouring halos in cache; fewer cells make windows too short to pay for
+   the ordering; the persistent queue overlaps windows). Results do not
+   depend on the order. */
+typedef enum {
+    FSKMC_ORDER_NATURAL = 0,
+    FSKMC_ORDER_WORKLOAD = 1,
+    FSKMC_ORDER_AUTO = 2
+} fskmc_task_order;
+fskmc_status fskmc_set_task_order(fskmc_ctx *ctx, fskmc_task_order order);
+
 /* Persistent engine: how many times a cell polls a neighbour's progress
    before giving up (default 2^20; polls back off to one per 4 us, so about
    4 s). A run whose wait gives up returns FSKMC_ETIMEOUT and leaves the

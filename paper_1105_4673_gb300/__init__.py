@@ -26,13 +26,14 @@ MODELS = {"ADSDES": 0, "ISING": 1, "ISING_ARRHENIUS": 1, "DIFFUSION": 2, "ADSDES
 SCHEMES = {"LIE": 0, "STRANG": 1, "RANDOM": 2, "RANDOM_ORDER": 3}
 CLOCKS = {"FP64": 0, "FP32": 1}
 ENGINES = {"PLAIN": 0, "PERSISTENT": 1}
+ORDERS = {"NATURAL": 0, "WORKLOAD": 1, "AUTO": 2}
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE"}
 
 # Every entry point the header declares (checked by the tests).
 EXPORTS = [
     "fskmc_create", "fskmc_batch_create", "fskmc_destroy", "fskmc_last_error",
     "fskmc_set_replica_id", "fskmc_set_clock", "fskmc_set_engine", "fskmc_set_warps_per_block",
-    "fskmc_set_spin_limit", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
+    "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
     "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_schedule",
@@ -84,6 +85,7 @@ def lib():
             "fskmc_set_engine": ([vp, C.c_int], C.c_int),
             "fskmc_set_warps_per_block": ([vp, C.c_int32], C.c_int),
             "fskmc_set_spin_limit": ([vp, C.c_uint32], C.c_int),
+            "fskmc_set_task_order": ([vp, C.c_int], C.c_int),
             "fskmc_info": ([vp, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_init_random": ([vp, C.c_uint64, C.c_double], C.c_int),
             "fskmc_init_bump": ([vp, C.c_uint64, C.c_double, C.c_double, C.c_int32], C.c_int),
@@ -206,6 +208,10 @@ class Context:
 
     def set_spin_limit(self, polls: int):
         _check(lib().fskmc_set_spin_limit(self.h, polls), self.h)
+
+    def set_task_order(self, order):
+        o = ORDERS[order] if isinstance(order, str) else int(order)
+        _check(lib().fskmc_set_task_order(self.h, o), self.h)
 
     def info(self) -> dict:
         out = (C.c_int32 * 5)()

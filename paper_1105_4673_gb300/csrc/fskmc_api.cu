@@ -42,6 +42,10 @@ struct fskmc_ctx {
     fskmc_engine engine = FSKMC_ENGINE_PLAIN;
     int wpb = 2;
     uint32_t spin_limit = 1u << 20;
+    fskmc_task_order order = FSKMC_ORDER_AUTO;
+    int nsm = 152;                       // SMs of the context's device
+    int32_t *d_order = nullptr;          // issue lists, total_cells entries
+    int32_t *d_order_scratch = nullptr;  // bucket histograms and cursors
     cudaStream_t stream = nullptr;
     fskmc::PersistentState *pers = nullptr;
     std::string err;
@@ -315,6 +319,12 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
     c->batch = batch;
     c->packed = lats[0].bitpacked != 0;
     c->stream = (cudaStream_t)stream;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            c->nsm = nsm;
+    }
     c->reps.resize(n);
     int64_t off = 0;
     int32_t coff = 0;
@@ -377,8 +387,50 @@ fskmc_status upload_reps(fskmc_ctx *c)
 }
 
 // One window of every replica on the plain engine.
+// Replicas per call of the ordering kernels (bounds their scratch).
+constexpr int ORDER_GROUP = 1024;
+
+// Heaviest-first issue lists for windows with `active` active cells: always
+// (WORKLOAD), never (NATURAL), or (AUTO) in the plain engine when a window's
+// cells fill the GPU in one wave (8 to 16 per SM): then the block
+// scheduler's round-robin over SMs spreads the heavy cells evenly. With
+// several waves of cells the scheduler balances by itself and row-major
+// order keeps neighbouring halos in cache; with few cells the windows are
+// too short to pay for the ordering launch; the persistent engine's queue
+// overlaps windows.
+bool use_order(const fskmc_ctx *c, int64_t active, bool persistent)
+{
+    if (c->order == FSKMC_ORDER_WORKLOAD) return true;
+    if (c->order == FSKMC_ORDER_NATURAL) return false;
+    return !persistent && active >= (int64_t)c->nsm * 8 && active <= (int64_t)c->nsm * 16;
+}
+
+fskmc_status ensure_order_buffers(fskmc_ctx *c)
+{
+    if (c->d_order) return FSKMC_OK;
+    const size_t scratch = (size_t)std::min(c->nrep, ORDER_GROUP) * 2 * fskmc::ORDER_BUCKETS * 2;
+    CK(c, cudaMalloc(&c->d_order, sizeof(int32_t) * (size_t)c->total_cells));
+    CK(c, cudaMalloc(&c->d_order_scratch, sizeof(int32_t) * scratch));
+    return FSKMC_OK;
+}
+
+// Issue lists of replicas [r0, r0 + n) for colours c0..c1.
+fskmc_status build_order(fskmc_ctx *c, int r0, int n, int c0, int c1)
+{
+    fskmc_status st = ensure_order_buffers(c);
+    if (st) return st;
+    const size_t half = (size_t)std::min(c->nrep, ORDER_GROUP) * 2 * fskmc::ORDER_BUCKETS;
+    for (int g = r0; g < r0 + n; g += ORDER_GROUP) {
+        const int ng = std::min(ORDER_GROUP, r0 + n - g);
+        CK(c, fskmc::launch_order(c->reps.data(), c->d_reps, g, ng, c0, c1, c->qx, c->qy,
+                                  c->d_workload, c->d_order, c->d_order_scratch,
+                                  c->d_order_scratch + half, c->stream));
+    }
+    return FSKMC_OK;
+}
+
 fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sched, size_t i,
-                          uint64_t w, uint64_t seed)
+                          uint64_t w, uint64_t seed, bool ordered)
 {
     const int fp32 = c->clock == FSKMC_CLOCK_FP32;
     const bool pingpong = c->d_lat[1] != nullptr;
@@ -397,8 +449,10 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         a.workload = c->d_workload;
         a.counters = c->d_counters;
         a.packed = c->packed ? 1 : 0;
+        a.order = nullptr;
         const Replica &R = c->reps[r];
         int nactive = R.ncx * R.ncy / 2;
+        if (ordered) a.order = c->d_order + R.cell_off + (size_t)win.colour * nactive;
         CK(c, fskmc::launch_window(c->model, fp32, a, nactive, c->wpb, c->stream));
     }
     if (pingpong) c->cur ^= 1;
@@ -438,6 +492,12 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         pr.wpb = std::min(c->wpb, 8);  // the persistent kernel is built for <= 256 threads
         pr.spin_limit = c->spin_limit;
         pr.packed = c->packed;
+        pr.order = nullptr;
+        if (use_order(c, c->total_cells / 2, true)) {
+            fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
+            if (st) return st;
+            pr.order = c->d_order;
+        }
         std::string msg;
         cudaError_t e = fskmc::persistent_run(&c->pers, pr, c->stream, &msg);
         if (e == cudaErrorTimeout) {
@@ -448,8 +508,16 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         if (e != cudaSuccess) return fail(c, FSKMC_ECUDA, "persistent run: %s (%s)", cudaGetErrorString(e), msg.c_str());
         if (c->d_lat[1] && (nw & 1)) c->cur ^= 1;
     } else {
+        // issue lists from the workloads at the start of the run
+        int64_t most = 0;
+        for (const Replica &R : c->reps) most = std::max<int64_t>(most, R.ncx * R.ncy / 2);
+        const bool ordered = use_order(c, most, false);
+        if (ordered) {
+            fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
+            if (st) return st;
+        }
         for (size_t i = 0; i < nw; ++i) {
-            fskmc_status st = plain_window(c, sched, i, c->w + i, seed);
+            fskmc_status st = plain_window(c, sched, i, c->w + i, seed, ordered);
             if (st) return st;
         }
     }
@@ -503,6 +571,8 @@ void fskmc_destroy(fskmc_ctx *c)
     cudaFree(c->d_scratch_u32);
     cudaFree(c->d_stage);
     cudaFree(c->d_obs);
+    cudaFree(c->d_order);
+    cudaFree(c->d_order_scratch);
     delete c;
 }
 
@@ -545,6 +615,14 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *c, int32_t warps)
     size_t need = fskmc::window_smem_per_warp(c->model, c->qx, c->qy) * (size_t)warps;
     if (need > 200 * 1024) return fail(c, FSKMC_EINVAL, "%d warps need %zu B of shared memory", warps, need);
     c->wpb = warps;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_task_order(fskmc_ctx *c, fskmc_task_order order)
+{
+    if (!c) return FSKMC_EINVAL;
+    if ((int)order < 0 || (int)order > 2) return fail(c, FSKMC_EINVAL, "unknown task order %d", (int)order);
+    c->order = order;
     return FSKMC_OK;
 }
 

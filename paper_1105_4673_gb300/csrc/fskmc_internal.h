@@ -67,6 +67,7 @@ struct WindowArgs {
     int32_t *workload;         // events per cell in its latest window
     unsigned long long *counters;  // [0] events, [1] ambiguous cell-windows, [2] timeouts
     int32_t packed;            // lattice stored 1 bit per site (spin-flip models)
+    const int32_t *order;      // active cells of the window (cell ids) in issue order, or null
 };
 
 // Shared-memory bytes one warp of the window kernel needs.
@@ -92,6 +93,17 @@ cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
 // in bit x % 32 of word y * lx/32 + x/32 (lx a multiple of 32).
 cudaError_t launch_pack(const uint8_t *bytes, uint32_t *words, int lx, int ly, cudaStream_t s);
 cudaError_t launch_unpack(const uint32_t *words, uint8_t *bytes, int lx, int ly, cudaStream_t s);
+
+// Workload-ordered issue lists (heaviest first by the per-cell event counts
+// of each cell's previous window). For replicas r0 .. r0+nrep-1 and the
+// colours in [c0, c1]: order[R.cell_off + c * ncells/2 + u] = the u-th
+// active cell of colour c in descending workload (bucketed: exact below 64
+// events, 8 buckets per power of two above). hist/cursor: scratch of
+// ORDER_BUCKETS * nrep * 2 ints each, cleared by the call.
+constexpr int ORDER_BUCKETS = 264;
+cudaError_t launch_order(const Replica *reps_host, const Replica *reps_dev, int r0, int nrep,
+                         int c0, int c1, int qx, int qy, const int32_t *workload, int32_t *order,
+                         int32_t *hist, int32_t *cursor, cudaStream_t s);
 
 // Self-test of the window kernel's integer-pipe division against the
 // hardware correctly rounded divide: counts disagreeing pairs into *bad.

@@ -1,4 +1,6 @@
 // Initial states, lattice validation and the integer observables of Section 7.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "fskmc_internal.h"
@@ -137,6 +139,150 @@ __global__ void observables_kernel(const uint8_t *lat, int lx, int ly, int rmax,
         if (acc[i]) atomicAdd(&out[i], (unsigned long long)acc[i]);
 }
 
+// Issue-order buckets of a cell's event count W: exact below 64, then 8
+// buckets per power of two (descending bucket = heavier).
+__device__ __forceinline__ int order_bucket(int32_t W)
+{
+    if (W < 64) return W < 0 ? 0 : W;
+    const int e = 31 - __clz(W);  // 6..30
+    return 64 + (e - 6) * 8 + ((W >> (e - 3)) & 7);
+}
+
+constexpr int ORDER_CHUNK = 4096;  // active cells per block
+constexpr int ORDER_THREADS = 512;
+
+// The u-th active cell of colour col in row-major order.
+__device__ __forceinline__ int active_cell(const Replica &R, int col, int u)
+{
+    const int half = R.ncx >> 1;
+    const int cy = u / half;
+    return cy * R.ncx + 2 * (u - cy * half) + ((col + cy) & 1);
+}
+
+// Block-local histogram of the buckets of this block's chunk of active cells.
+__device__ void order_local_hist(const Replica &R, int col, int u0, int n, const int32_t *wl,
+                                 int32_t *h)
+{
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int u1 = min(n, u0 + ORDER_CHUNK);
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x)
+        atomicAdd(&h[order_bucket(wl[R.cell_off + active_cell(R, col, u)])], 1);
+    __syncthreads();
+}
+
+__global__ void order_hist_kernel(const Replica *reps, int r0, int c0, const int32_t *wl,
+                                  int32_t *hist)
+{
+    __shared__ int32_t h[ORDER_BUCKETS];
+    const Replica &R = reps[r0 + blockIdx.y];
+    const int col = c0 + blockIdx.z;
+    const int n = (R.ncx >> 1) * R.ncy;
+    const int u0 = blockIdx.x * ORDER_CHUNK;
+    if (u0 >= n) return;  // uniform over the block
+    order_local_hist(R, col, u0, n, wl, h);
+    int32_t *gh = hist + ((size_t)blockIdx.y * 2 + blockIdx.z) * ORDER_BUCKETS;
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+        if (h[i]) atomicAdd(&gh[i], h[i]);
+}
+
+__global__ void order_scatter_kernel(const Replica *reps, int r0, int c0, const int32_t *wl,
+                                     const int32_t *hist, int32_t *cursor, int32_t *order)
+{
+    __shared__ int32_t h[ORDER_BUCKETS], base[ORDER_BUCKETS];
+    const Replica &R = reps[r0 + blockIdx.y];
+    const int col = c0 + blockIdx.z;
+    const int n = (R.ncx >> 1) * R.ncy;
+    const int u0 = blockIdx.x * ORDER_CHUNK;
+    if (u0 >= n) return;
+    order_local_hist(R, col, u0, n, wl, h);
+    const size_t seg = ((size_t)blockIdx.y * 2 + blockIdx.z) * ORDER_BUCKETS;
+    // bucket b starts after every heavier bucket: exclusive scan in
+    // descending bucket order, 9 buckets per lane of warp 0
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int v[9], sum = 0;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int d = lane * 9 + t, b = ORDER_BUCKETS - 1 - d;
+            v[t] = d < ORDER_BUCKETS ? hist[seg + b] : 0;
+            sum += v[t];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += x;
+        }
+        int acc = incl - sum;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int d = lane * 9 + t;
+            if (d < ORDER_BUCKETS) base[ORDER_BUCKETS - 1 - d] = acc;
+            acc += v[t];
+        }
+    }
+    __syncthreads();
+    // reserve this block's range in every bucket it uses
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x)
+        if (h[i]) base[i] += atomicAdd(&cursor[seg + i], h[i]);
+    __syncthreads();
+    int32_t *out = order + R.cell_off + (size_t)col * n;
+    const int u1 = min(n, u0 + ORDER_CHUNK);
+    for (int u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+        const int m = active_cell(R, col, u);
+        out[atomicAdd(&base[order_bucket(wl[R.cell_off + m])], 1)] = m;
+    }
+}
+
+// Whole issue list of one (replica, colour) in one block, for windows of at
+// most ORDER_SINGLE active cells: histogram, scan and scatter in shared
+// memory, no global scratch.
+constexpr int ORDER_SINGLE = 32768;
+
+__global__ void order_single_kernel(const Replica *reps, int r0, int c0, const int32_t *wl,
+                                    int32_t *order)
+{
+    __shared__ int32_t h[ORDER_BUCKETS], base[ORDER_BUCKETS];
+    const Replica &R = reps[r0 + blockIdx.x];
+    const int col = c0 + blockIdx.y;
+    const int n = (R.ncx >> 1) * R.ncy;
+    for (int i = threadIdx.x; i < ORDER_BUCKETS; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (int u = threadIdx.x; u < n; u += blockDim.x)
+        atomicAdd(&h[order_bucket(wl[R.cell_off + active_cell(R, col, u)])], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan, heaviest bucket first
+        const int lane = threadIdx.x;
+        int v[9], sum = 0;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int d = lane * 9 + t;
+            v[t] = d < ORDER_BUCKETS ? h[ORDER_BUCKETS - 1 - d] : 0;
+            sum += v[t];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int x = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += x;
+        }
+        int acc = incl - sum;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int d = lane * 9 + t;
+            if (d < ORDER_BUCKETS) base[ORDER_BUCKETS - 1 - d] = acc;
+            acc += v[t];
+        }
+    }
+    __syncthreads();
+    int32_t *out = order + R.cell_off + (size_t)col * n;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        const int m = active_cell(R, col, u);
+        out[atomicAdd(&base[order_bucket(wl[R.cell_off + m])], 1)] = m;
+    }
+}
+
 int grid_for(int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
@@ -179,6 +325,34 @@ cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
     size_t smem = sizeof(unsigned int) * (size_t)(4 + 2 * rmax);
     if (packed) observables_kernel<true><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
     else observables_kernel<false><<<grid, 256, smem, s>>>(lat, lx, ly, rmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order(const Replica *reps_host, const Replica *reps_dev, int r0, int nrep,
+                         int c0, int c1, int qx, int qy, const int32_t *workload, int32_t *order,
+                         int32_t *hist, int32_t *cursor, cudaStream_t s)
+{
+    (void)qx;
+    (void)qy;
+    if (nrep < 1 || nrep > 65535 || c0 < 0 || c1 > 1 || c0 > c1) return cudaErrorInvalidValue;
+    int64_t most = 0;
+    for (int r = r0; r < r0 + nrep; ++r)
+        most = std::max<int64_t>(most, (int64_t)(reps_host[r].ncx / 2) * reps_host[r].ncy);
+    if (most == 0) return cudaSuccess;
+    if (most <= ORDER_SINGLE) {
+        order_single_kernel<<<dim3((unsigned)nrep, (unsigned)(c1 - c0 + 1)), 1024, 0, s>>>(
+            reps_dev, r0, c0, workload, order);
+        return cudaGetLastError();
+    }
+    const size_t words = (size_t)nrep * 2 * ORDER_BUCKETS;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * words, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * words, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((most + ORDER_CHUNK - 1) / ORDER_CHUNK), (unsigned)nrep,
+                    (unsigned)(c1 - c0 + 1));
+    order_hist_kernel<<<grid, ORDER_THREADS, 0, s>>>(reps_dev, r0, c0, workload, hist);
+    order_scatter_kernel<<<grid, ORDER_THREADS, 0, s>>>(reps_dev, r0, c0, workload, hist, cursor,
+                                                        order);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ struct PersistentRun {
     uint64_t w0, seed;
     uint32_t spin_limit;          // polls before a wait gives up
     bool packed;                  // bit-packed lattice (spin-flip models)
+    const int32_t *order;         // device: active cells per replica and colour, heaviest
+                                  // first (see launch_order), or null for row-major order
 };
 
 struct PersistentState;  // device buffers and the captured CUDA graph

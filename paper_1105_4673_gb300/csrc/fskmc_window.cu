@@ -857,9 +857,16 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
     const int g = blockIdx.x * (blockDim.x >> 5) + wib;
     if (g >= nactive) return;
     const Replica &R = a.reps[a.rep_index];
-    const int half = R.ncx >> 1;
-    const int cy = g / half;
-    const int cx = 2 * (g % half) + ((a.colour + cy) & 1);
+    int cx, cy;
+    if (a.order) {  // heaviest-first issue list
+        const int m = a.order[g];
+        cy = m / R.ncx;
+        cx = m - cy * R.ncx;
+    } else {
+        const int half = R.ncx >> 1;
+        cy = g / half;
+        cx = 2 * (g % half) + ((a.colour + cy) & 1);
+    }
     const uint8_t *src = a.src + R.lat_off;
     uint8_t *dst = a.dst + R.lat_off;
     if (a.src != a.dst) {
@@ -911,6 +918,7 @@ struct PParams {
     const int8_t *colour;
     int32_t colour_per_replica;
     const int2 *prev;          // per (replica,) window: last earlier window of the same / other colour
+    const int32_t *order;      // per replica and colour: active cells heaviest first, or null
     int32_t inplace;           // in-place models: only active cells have tasks
     const double *h;
     int64_t nwin;
@@ -991,9 +999,16 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
         const int wcol = P.colour[widx];
         const int ccol = active ? wcol : 1 - wcol;
-        const int half = R.ncx >> 1;
-        const int cy = k / half;
-        const int cx = 2 * (k % half) + ((ccol + cy) & 1);
+        int cx, cy;
+        if (active && P.order) {
+            const int mo = P.order[R.cell_off + ccol * ((R.ncx >> 1) * R.ncy) + k];
+            cy = mo / R.ncx;
+            cx = mo - cy * R.ncx;
+        } else {
+            const int half = R.ncx >> 1;
+            cy = k / half;
+            cx = 2 * (k % half) + ((ccol + cy) & 1);
+        }
         const int m = cy * R.ncx + cx;
         int32_t *ep = P.epoch + R.cell_off;
         uint8_t *cur = (pingpong && (i & 1)) ? P.lat2 : P.lat;
@@ -1262,6 +1277,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     P.colour = st->d_colour;
     P.colour_per_replica = run.colour_per_replica ? 1 : 0;
     P.prev = st->d_prev;
+    P.order = run.order;
     P.inplace = run.lat2 == nullptr ? 1 : 0;
     P.h = st->d_h;
     P.nwin = run.nwin;

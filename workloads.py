@@ -11,11 +11,12 @@ import numpy as np
 
 SEED_BASE = 0x5EED0000
 
-# The five workloads. Sizes, rates and schedules follow the paper's test
+# The six workloads. Sizes, rates and schedules follow the paper's test
 # problems: non-interacting and interacting adsorption/desorption (Section 4.1),
 # the 2D Ising benchmark (Section 7), adsorption/desorption with surface
 # diffusion (Section 2), an ensemble of replicas (Section 7's M independent
-# realisations) and the ZGB catalysis model (Section 7.1).
+# realisations), the ZGB catalysis model (Section 7.1) and the 1D Ising ring
+# (Section 7).
 WORKLOADS = {
     "adsdes64": dict(lx=64, ly=64, model="ADSDES", rates=dict(ka=1.0, kd=1.0, betaJ=1.0),
                      q=(8, 8), scheme="LIE", dt=0.1, T=10.0, coverage=0.5,
@@ -32,7 +33,19 @@ WORKLOADS = {
     "zgb16384": dict(lx=16384, ly=16384, model="ZGB",
                      rates=dict(yA=0.52, kr=100.0, kd=0.01), q=(32, 32), scheme="STRANG",
                      dt=0.02, T=200.0, bump=dict(amp=0.9, width=16384 / 8), seed=SEED_BASE + 4),
+    # the 1D Ising benchmark of Section 7: a ring of N = 2^15 sites, K = 1,
+    # beta = 4, h = 1 (betaJ = beta K, betah = beta h), dt = 1.0
+    "ising1d32768": dict(lx=32768, ly=1, model="ISING1D",
+                         rates=dict(ka=1.0, kd=1.0, betaJ=4.0, betah=4.0), q=(32, 1),
+                         scheme="LIE", dt=1.0, T=1000.0, coverage=0.5, bitpacked=True,
+                         seed=SEED_BASE + 5),
 }
+
+
+def sample_shape(w: dict) -> tuple[int, int]:
+    """A bounded sample of a workload for the host-CPU oracle timing: a
+    256 x 256 lattice, or a ring of 8192 sites for the 1D model."""
+    return (8192, 1) if w["model"] == "ISING1D" else (256, 256)
 
 
 def ensemble_replicas(n: int = 512, seed: int = SEED_BASE + 3):
