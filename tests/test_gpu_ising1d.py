@@ -145,3 +145,52 @@ def test_phase_diagram_and_correlation_n2_15():
             for r in range(1, rmax + 1):
                 want_g = CF.ising1d_covariance(b, b * h, r) + th * th
                 assert abs(g[:, r - 1].mean() - want_g) < 5 * seg[r - 1] + 0.01, (b, r)
+
+
+def _coverage_paths(dt, M, T, start, seed):
+    """Coverage of M independent rings of 2^15 sites (beta = 4, h = 1, K = 1)
+    sampled once per time unit for T units."""
+    L = 1 << 15
+    batch = [dict(lx=L, ly=1, rates=_rates(4.0, 1.0)) for _ in range(M)]
+    S = np.zeros((T + 1, M))
+    with F.Context(model="ISING1D", q=(1024, 1), batch=batch) as c:
+        c.set_engine("PERSISTENT")
+        c.set_clock("FP32")
+        c.init_random(seed, start)
+        S[0] = [c.observables(r, 0)[0][1] for r in range(M)]
+        for k in range(1, T + 1):
+            c.run("LIE", dt, 1.0, seed)
+            S[k] = [c.observables(r, 0)[0][1] for r in range(M)]
+    return S
+
+
+def _autocorr(S, burn, lags):
+    X = S[burn:] - S[burn:].mean(axis=0)
+    v = (X * X).mean()
+    return np.array([(X[:len(X) - k] * X[k:]).mean() / v for k in lags])
+
+
+def test_coverage_process_converges_in_dt():
+    """Fig. samples1D: the total-coverage process of 256 realisations at
+    beta = 4, h = 1 on N = 2^15 (binary32 clock). Its mean and spread along
+    the relaxation from the empty lattice, and its autocorrelation in
+    equilibrium, at dt = 1.0 and 0.1 against dt = 0.01 (the serial-SSA
+    limit of the splitting). Means by z-score; the autocorrelation within
+    0.05."""
+    M, T = 256, 40
+    ref = _coverage_paths(0.01, M, T, 0.0, 31)
+    for dt in (1.0, 0.1):
+        S = _coverage_paths(dt, M, T, 0.0, 32 if dt == 1.0 else 33)
+        se = np.sqrt(S[1:].var(axis=1, ddof=1) / M + ref[1:].var(axis=1, ddof=1) / M)
+        z = (S[1:].mean(axis=1) - ref[1:].mean(axis=1)) / se
+        assert np.abs(z).max() < 4.5, (dt, z)
+        # spread across realisations within 25% of the reference
+        ratio = S[5:].std(axis=1) / ref[5:].std(axis=1)
+        assert np.all(np.abs(ratio - 1) < 0.25), (dt, ratio)
+    lags = [0, 1, 2, 5, 10, 20]
+    acs = {}
+    for dt, seed in ((0.01, 41), (0.1, 42), (1.0, 43)):
+        acs[dt] = _autocorr(_coverage_paths(dt, M, 300, 0.5, seed), 100, lags)
+    assert acs[0.01][1] > 0.3  # the process is visibly correlated over one time unit
+    for dt in (0.1, 1.0):
+        assert np.abs(acs[dt] - acs[0.01]).max() < 0.05, (dt, acs[dt], acs[0.01])
