@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--wpb", type=int, default=0, help="warps per CTA (0: the library default)")
     p.add_argument("--order", default="auto", choices=["auto", "natural", "workload"],
                    help="issue order of a window's active cells")
+    p.add_argument("--grouping", default="auto", choices=["auto", "on", "off"],
+                   help="several small spin-flip cells per warp (on), one cell per warp (off), "
+                        "or the library's choice (auto)")
     return p.parse_args()
 
 
@@ -238,6 +241,7 @@ def main():
     if args.wpb:
         ctx.set_warps_per_block(args.wpb)
     ctx.set_task_order(args.order.upper())
+    ctx.set_cell_grouping({"auto": "AUTO", "on": True, "off": False}[args.grouping])
     init_state(ctx, w, seed)
     step_t = STEP_WINDOWS_DT * w["dt"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -339,7 +343,8 @@ def main():
                    "step": f"{step_t:g} time units ({kernel_windows_per_step(F, w, step_t)} windows) "
                            "+ observables",
                    "clock": args.clock, "engine": args.engine,
-                   "warps_per_cta": ctx.info()["warps_per_block"], "task_order": args.order,
+                   "warps_per_cta": ctx.info()["warps_per_block"],
+                   "lanes_per_cell": ctx.info()["lanes_per_cell"], "task_order": args.order,
                    "storage": "1 bit/site" if w.get("bitpacked") else "1 byte/site",
                    "l2": "flushed between timed steps"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
@@ -374,11 +379,15 @@ def measure_variants(F, w, stream, seed, steps):
     res["ensemble512_persistent_fp32"] = ensemble_rate(F, stream, "FP32")
     res["ensemble512_persistent_fp64"] = ensemble_rate(F, stream, "FP64")
     res["fp32_vs_fp64"] = clock_error(F, stream, w)
-    for engine, clock in (("PERSISTENT", "FP64"), ("PERSISTENT", "FP32"), ("PLAIN", "FP32")):
+    forms = [("PERSISTENT", "FP64", "AUTO"), ("PERSISTENT", "FP32", "AUTO"), ("PLAIN", "FP32", "AUTO")]
+    if _group_width_default(F, w) < 32:  # the same workload with one cell per warp
+        forms += [("PLAIN", "FP64", False)]
+    for engine, clock, grouped in forms:
         c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream,
                       bitpacked=w.get("bitpacked", False))
         c.set_engine(engine)
         c.set_clock(clock)
+        c.set_cell_grouping(grouped)
         init_state(c, w, seed)
         step_t = STEP_WINDOWS_DT * w["dt"]
         c.run(w["scheme"], w["dt"], step_t, seed)
@@ -391,10 +400,20 @@ def measure_variants(F, w, stream, seed, steps):
         b.record(stream)
         torch.cuda.synchronize()
         ev = c.stats()["events"] - e0
-        res[f"{engine.lower()}_{clock.lower()}"] = {"events_per_s": ev / (a.elapsed_time(b) / 1000),
-                                                    "events": ev}
+        key = f"{engine.lower()}_{clock.lower()}" + ("" if grouped else "_one_cell_per_warp")
+        res[key] = {"events_per_s": ev / (a.elapsed_time(b) / 1000), "events": ev,
+                    "lanes_per_cell": c.info()["lanes_per_cell"]}
         c.close()
     return res
+
+
+def _group_width_default(F, w):
+    """Lanes per cell the library picks for the workload's cells."""
+    c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"],
+                  bitpacked=w.get("bitpacked", False))
+    n = c.info()["lanes_per_cell"]
+    c.close()
+    return n
 
 
 def ensemble_rate(F, stream, clock, T=5.0):

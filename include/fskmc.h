@@ -152,9 +152,24 @@ fskmc_status fskmc_set_replica_id(fskmc_ctx *ctx, uint32_t id);
 fskmc_status fskmc_set_clock(fskmc_ctx *ctx, fskmc_clock clock);
 fskmc_status fskmc_set_engine(fskmc_ctx *ctx, fskmc_engine engine);
 
-/* Launch shape of the window kernels: warps (= cells) per block, 1..16.
-   Results do not depend on it. */
+/* Launch shape of the window kernels: warps per block, 1..16 (a warp runs
+   one cell, or several small cells when grouped, below). Results do not
+   depend on it. */
 fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
+
+/* Cells per warp for the spin-flip models (ADSDES, ISING, ISING1D).
+   mode = 1: a cell of at most 512 sites takes W = 4, 8 or 16 lanes (its
+   32-site words rounded up to a power of two; at least 8 in 2D, 4 on a
+   ring) and a warp runs 32/W cells of the same window in lockstep, so each
+   instruction of the event loop (Eqs. totalrate and skeleton per cell)
+   serves 32/W cells. mode = 0: one
+   cell per warp. mode = 2 (default, auto): grouped when a window's active
+   cells are more than one wave of one-cell warps on the device, and in the
+   plain engine with the binary64 clock; otherwise one cell per warp. The
+   two-site models and larger cells always take a whole warp. Results
+   (lattices, event counts, workloads) do not depend on the mode. EINVAL:
+   mode outside 0..2. */
+fskmc_status fskmc_set_cell_grouping(fskmc_ctx *ctx, int32_t mode);
 
 /* Order in which the active cells of a window are issued (Section 6,
    Eq. wload). The paper rebalances by reshaping the cells so that each
@@ -185,8 +200,10 @@ fskmc_status fskmc_set_task_order(fskmc_ctx *ctx, fskmc_task_order order);
 fskmc_status fskmc_set_spin_limit(fskmc_ctx *ctx, uint32_t polls);
 
 /* Effective cell shape and sizes: out[0]=qx, out[1]=qy, out[2]=replicas,
-   out[3]=total cells over replicas, out[4]=warps per block. */
-fskmc_status fskmc_info(const fskmc_ctx *ctx, int32_t out[5]);
+   out[3]=total cells over replicas, out[4]=warps per block, out[5]=lanes per
+   cell the window kernels use with the current engine, clock and grouping
+   mode (32: one cell per warp). */
+fskmc_status fskmc_info(const fskmc_ctx *ctx, int32_t out[6]);
 
 /*
  * Bernoulli(coverage) initial state of every replica: site i of replica r
@@ -279,16 +296,30 @@ fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);
 fskmc_status fskmc_sync(fskmc_ctx *ctx);
 
 /*
- * Self-test of the binary64 window clock's divide. The waiting time
+ * Self-test of the binary64 window clock's divides. The waiting time
  * -log(u_t)/lambda of the binary64 contract (Eqs. totalrate/skeleton) is
- * computed on the integer pipes (exact quotient and remainder of the
- * significands, rounded to nearest even); this compares it with the
+ * divided without the hardware divide: on the integer pipes (exact quotient
+ * and remainder of the significands, rounded to nearest even; one-cell
+ * kernels) or by a Newton-Raphson reciprocal with an exact integer
+ * correction of the quotient (grouped kernels). This compares both with the
  * hardware correctly rounded divide on the n pairs (a[i] >= 0, b[i] > 0,
- * host arrays) and writes the number of disagreeing pairs to *mismatches
- * (must be 0). Runs on the current device. EINVAL: NULL pointers, n < 0.
+ * host arrays) and writes the number of disagreements (over both methods)
+ * to *mismatches (must be 0). Runs on the current device. EINVAL: NULL
+ * pointers, n < 0.
  */
 fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
                                    uint32_t *mismatches);
+
+/*
+ * Self-test of the binary64 window clock's logarithm. The waiting-time
+ * numerator -log(u_t), u_t = n 2^-53 (Eqs. totalrate/skeleton with the draw
+ * of u_t in (0, 1]), is computed by a table-driven logarithm (Tang's
+ * reduction); this writes the device's value for each n[i] (host arrays,
+ * 1 <= n[i] <= 2^53) to out[i] so that callers can compare it with a host
+ * logarithm. Runs on the current device. EINVAL: NULL pointers, count < 0,
+ * n[i] out of range.
+ */
+fskmc_status fskmc_selftest_log(const uint64_t *n, int32_t count, double *out);
 
 /*
  * Autotuner for the batched workload: for every square cell size q in

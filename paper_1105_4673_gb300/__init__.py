@@ -33,10 +33,11 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5:
 EXPORTS = [
     "fskmc_create", "fskmc_batch_create", "fskmc_destroy", "fskmc_last_error",
     "fskmc_set_replica_id", "fskmc_set_clock", "fskmc_set_engine", "fskmc_set_warps_per_block",
-    "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
+    "fskmc_set_cell_grouping", "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
-    "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_schedule",
+    "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_selftest_log",
+    "fskmc_schedule",
 ]
 NOALLOC_MAX_RMAX = 256
 
@@ -84,6 +85,7 @@ def lib():
             "fskmc_set_clock": ([vp, C.c_int], C.c_int),
             "fskmc_set_engine": ([vp, C.c_int], C.c_int),
             "fskmc_set_warps_per_block": ([vp, C.c_int32], C.c_int),
+            "fskmc_set_cell_grouping": ([vp, C.c_int32], C.c_int),
             "fskmc_set_spin_limit": ([vp, C.c_uint32], C.c_int),
             "fskmc_set_task_order": ([vp, C.c_int], C.c_int),
             "fskmc_info": ([vp, C.POINTER(C.c_int32)], C.c_int),
@@ -101,6 +103,7 @@ def lib():
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
             "fskmc_selftest_divide": ([vp, vp, C.c_int32, C.POINTER(C.c_uint32)], C.c_int),
+            "fskmc_selftest_log": ([vp, C.c_int32, vp], C.c_int),
             "fskmc_schedule": ([C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32, C.c_uint64,
                                 vp, vp, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
             "fskmc_autotune": ([C.c_int32, C.POINTER(Lattice), C.c_int, C.POINTER(Rates), C.c_int,
@@ -206,6 +209,11 @@ class Context:
     def set_warps_per_block(self, w: int):
         _check(lib().fskmc_set_warps_per_block(self.h, w), self.h)
 
+    def set_cell_grouping(self, mode):
+        """True / False / "AUTO" (the library default)."""
+        m = 2 if mode == "AUTO" else (1 if mode else 0)
+        _check(lib().fskmc_set_cell_grouping(self.h, m), self.h)
+
     def set_spin_limit(self, polls: int):
         _check(lib().fskmc_set_spin_limit(self.h, polls), self.h)
 
@@ -214,9 +222,10 @@ class Context:
         _check(lib().fskmc_set_task_order(self.h, o), self.h)
 
     def info(self) -> dict:
-        out = (C.c_int32 * 5)()
+        out = (C.c_int32 * 6)()
         _check(lib().fskmc_info(self.h, out), self.h)
-        return dict(qx=out[0], qy=out[1], replicas=out[2], cells=out[3], warps_per_block=out[4])
+        return dict(qx=out[0], qy=out[1], replicas=out[2], cells=out[3], warps_per_block=out[4],
+                    lanes_per_cell=out[5])
 
     # -- state -----------------------------------------------------------
     def init_random(self, seed: int, coverage: float):
@@ -301,6 +310,14 @@ def selftest_divide(a, b) -> int:
     bad = C.c_uint32()
     _check(lib().fskmc_selftest_divide(a.ctypes.data, b.ctypes.data, len(a), C.byref(bad)))
     return bad.value
+
+
+def selftest_log(n) -> np.ndarray:
+    """fskmc_selftest_log: the device's -log(n 2^-53) for integers n in [1, 2^53]."""
+    n = np.ascontiguousarray(n, np.uint64)
+    out = np.empty(len(n), np.float64)
+    _check(lib().fskmc_selftest_log(n.ctypes.data, len(n), out.ctypes.data))
+    return out
 
 
 def autotune(batch, model, scheme, dt, clock="FP32", engine="PERSISTENT", coverage=0.5,

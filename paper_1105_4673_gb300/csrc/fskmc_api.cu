@@ -41,6 +41,7 @@ struct fskmc_ctx {
     fskmc_clock clock = FSKMC_CLOCK_FP64;
     fskmc_engine engine = FSKMC_ENGINE_PLAIN;
     int wpb = 2;
+    int grouping = 2;      // several small cells per warp: 0 off, 1 on, 2 auto (spin-flip models)
     uint32_t spin_limit = 1u << 20;
     fskmc_task_order order = FSKMC_ORDER_AUTO;
     int nsm = 152;                       // SMs of the context's device
@@ -398,6 +399,32 @@ constexpr int ORDER_GROUP = 1024;
 // order keeps neighbouring halos in cache; with few cells the windows are
 // too short to pay for the ordering launch; the persistent engine's queue
 // overlaps windows.
+// Lanes per cell of the window kernels for this context and engine. AUTO
+// groups small cells when a window's active cells fill more than one wave of
+// one-cell warps (many warps then share each SM's issue slots and FP64 pipe,
+// and grouping divides that load), and in the plain engine with the binary64
+// clock (its FP64 pipe is busy even in one wave). A single wave in the
+// persistent engine keeps one cell per warp: there the cells of a warp would
+// wait for each other's neighbours, lengthening the chain of dependent
+// windows.
+int lanes_per_cell(const fskmc_ctx *c, bool persistent)
+{
+    const int W = fskmc::group_width(c->model, c->qx, c->qy);
+    if (W >= 32 || c->grouping == 0) return 32;
+    if (c->grouping == 1) return W;
+    const int fp32 = c->clock == FSKMC_CLOCK_FP32;
+    if (!persistent && !fp32) return W;
+    int64_t active = 0;
+    if (persistent) {
+        active = c->total_cells / 2;
+    } else {
+        for (const Replica &R : c->reps) active = std::max<int64_t>(active, (int64_t)R.ncx * R.ncy / 2);
+    }
+    const int wpb = persistent ? std::min(c->wpb, 8) : c->wpb;
+    const int resident = fskmc::window_resident_warps(c->model, fp32, c->packed, c->qx, c->qy, wpb);
+    return active > resident ? W : 32;
+}
+
 bool use_order(const fskmc_ctx *c, int64_t active, bool persistent)
 {
     if (c->order == FSKMC_ORDER_WORKLOAD) return true;
@@ -430,7 +457,7 @@ fskmc_status build_order(fskmc_ctx *c, int r0, int n, int c0, int c1)
 }
 
 fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sched, size_t i,
-                          uint64_t w, uint64_t seed, bool ordered)
+                          uint64_t w, uint64_t seed, bool ordered, int lanes)
 {
     const int fp32 = c->clock == FSKMC_CLOCK_FP32;
     const bool pingpong = c->d_lat[1] != nullptr;
@@ -450,6 +477,7 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         a.counters = c->d_counters;
         a.packed = c->packed ? 1 : 0;
         a.order = nullptr;
+        a.lanes_per_cell = lanes;
         const Replica &R = c->reps[r];
         int nactive = R.ncx * R.ncy / 2;
         if (ordered) a.order = c->d_order + R.cell_off + (size_t)win.colour * nactive;
@@ -492,6 +520,7 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         pr.wpb = std::min(c->wpb, 8);  // the persistent kernel is built for <= 256 threads
         pr.spin_limit = c->spin_limit;
         pr.packed = c->packed;
+        pr.lanes_per_cell = lanes_per_cell(c, true);
         pr.order = nullptr;
         if (use_order(c, c->total_cells / 2, true)) {
             fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
@@ -516,8 +545,9 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
             fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
             if (st) return st;
         }
+        const int lanes = lanes_per_cell(c, false);
         for (size_t i = 0; i < nw; ++i) {
-            fskmc_status st = plain_window(c, sched, i, c->w + i, seed, ordered);
+            fskmc_status st = plain_window(c, sched, i, c->w + i, seed, ordered, lanes);
             if (st) return st;
         }
     }
@@ -612,9 +642,18 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *c, int32_t warps)
 {
     if (!c) return FSKMC_EINVAL;
     if (warps < 1 || warps > 16) return fail(c, FSKMC_EINVAL, "warps per block must be 1..16");
-    size_t need = fskmc::window_smem_per_warp(c->model, c->qx, c->qy) * (size_t)warps;
+    size_t need = std::max(fskmc::window_smem_per_warp(c->model, c->qx, c->qy),
+                           fskmc::group_smem_per_warp(c->model, c->qx, c->qy)) * (size_t)warps;
     if (need > 200 * 1024) return fail(c, FSKMC_EINVAL, "%d warps need %zu B of shared memory", warps, need);
     c->wpb = warps;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_cell_grouping(fskmc_ctx *c, int32_t on)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (on < 0 || on > 2) return fail(c, FSKMC_EINVAL, "cell grouping must be 0 (off), 1 (on) or 2 (auto)");
+    c->grouping = on;
     return FSKMC_OK;
 }
 
@@ -633,7 +672,7 @@ fskmc_status fskmc_set_spin_limit(fskmc_ctx *c, uint32_t polls)
     return FSKMC_OK;
 }
 
-fskmc_status fskmc_info(const fskmc_ctx *c, int32_t out[5])
+fskmc_status fskmc_info(const fskmc_ctx *c, int32_t out[6])
 {
     if (!c || !out) return FSKMC_EINVAL;
     out[0] = c->qx;
@@ -641,6 +680,7 @@ fskmc_status fskmc_info(const fskmc_ctx *c, int32_t out[5])
     out[2] = c->nrep;
     out[3] = c->total_cells;
     out[4] = c->wpb;
+    out[5] = lanes_per_cell(c, c->engine == FSKMC_ENGINE_PERSISTENT);
     return FSKMC_OK;
 }
 
@@ -882,6 +922,24 @@ fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
     cudaFree(dbad);
     if (e != cudaSuccess) return fail(nullptr, FSKMC_ECUDA, "self-test: %s", cudaGetErrorString(e));
     *mismatches = bad;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_selftest_log(const uint64_t *nn, int32_t count, double *out)
+{
+    if (!nn || !out || count < 0) return fail(nullptr, FSKMC_EINVAL, "bad self-test arguments");
+    for (int32_t i = 0; i < count; ++i)
+        if (nn[i] < 1 || nn[i] > (1ull << 53)) return fail(nullptr, FSKMC_EINVAL, "n[%d] outside [1, 2^53]", i);
+    unsigned long long *dn = nullptr;
+    double *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dn, sizeof(unsigned long long) * (size_t)count + 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, sizeof(double) * (size_t)count + 8);
+    if (e == cudaSuccess) e = cudaMemcpy(dn, nn, sizeof(unsigned long long) * (size_t)count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = fskmc::launch_log_selftest(dn, count, dout, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost);
+    cudaFree(dn);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, FSKMC_ECUDA, "self-test: %s", cudaGetErrorString(e));
     return FSKMC_OK;
 }
 

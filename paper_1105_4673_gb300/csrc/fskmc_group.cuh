@@ -1,0 +1,513 @@
+// Grouped window kernels for the spin-flip models with small cells: one warp
+// runs 32/W cells of the same window at once, W lanes per cell (4, 8 or 16:
+// the lanes that own the cell's 32-site words, rounded up to a power of two,
+// and at least the lanes one flip's class refresh uses: 5 in 2D, 3 on a ring).
+//
+// Why: a cell's serial SSA (Eqs. totalrate and skeleton) is a chain of
+// warp-uniform steps -- the class sums, the waiting time, the class choice --
+// and on GB300 an FP64 warp instruction costs the FP64 pipe the same whether
+// one lane or 32 execute it (the issue slot likewise). A 16x16 cell has 256
+// sites, 8 lanes' worth of 32-site words, so a one-cell warp leaves 24 lanes
+// idle in every step. Here the cells of a warp share every instruction.
+//
+// The groups of a warp run in lockstep: every loop iteration executes one
+// event of each group whose window is still running; a group whose window
+// has ended (waiting time past the edge, no rate left) stays in the loop
+// with its side effects switched off until every group is done. Each group's
+// draws, arithmetic and member order are exactly those of the one-cell
+// kernel (fskmc_window.cu), so results are bit-identical to it and to the
+// oracle: the same Philox counters (event index, window, cell, replica), the
+// same ordered binary64 fused multiply-add chain or exact fixed-point sums,
+// the same rank search in canonical (lane-major) order.
+//
+// Cells in a warp are independent: they are same-colour cells of one window
+// (Eq. exact: their generators commute), each with its own shared-memory
+// region; only warp-wide votes and width-W shuffles are shared.
+#pragma once
+#include <cuda/atomic>
+#include <cuda_runtime.h>
+
+#include "fskmc_device.cuh"
+#include "fskmc_internal.h"
+
+namespace fskmc {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Per-cell shared memory: the cell and its halo (one byte per site), the
+// class code of every own site, KS x W membership words (word l of class k
+// holds sites 32l .. 32l+31, owned by lane l), 16 class counts, the counts
+// as binary64. Cells are spaced a multiple of 128 bytes plus W words apart,
+// so the cells' words at the same offset fall in different banks.
+struct GLayout {
+    int BW, BH, nsite;
+    int scls_off, mask_off, cnt_off, dcnt_off;
+    int stride;
+};
+
+template <int MODEL>
+__host__ __device__ inline GLayout make_glayout(int qx, int qy, int W)
+{
+    using TR = Traits<MODEL>;
+    GLayout L;
+    L.BW = qx + 2 * TR::HW;
+    L.BH = qy + 2 * TR::HW;
+    L.nsite = qx * qy;
+    int o = (L.BW * L.BH + 15) & ~15;
+    L.scls_off = o;
+    o += (L.nsite + 15) & ~15;
+    L.mask_off = o;
+    o += 4 * TR::KS * W;
+    L.cnt_off = o;
+    o += 4 * MAX_CLASSES;
+    L.dcnt_off = o;
+    o += 8 * MAX_CLASSES;
+    L.stride = ((o + 127) & ~127) + 4 * W;
+    return L;
+}
+
+// One group's fractional window (W lanes; every lane of the warp calls this
+// together). valid = the group has a cell. Outputs (group-uniform): events,
+// whether an edge decision was ambiguous, whether a consistency check failed.
+// The class data are lane-parallel: lane l holds classes l, l + W, ... for
+// the fixed-point prefix sums (width-W shuffle scans), converts their counts
+// to binary64 for the ordered fused multiply-add chain (which every lane then
+// runs), and owns membership word l for the rank search.
+template <int MODEL, typename CLK, bool PERSIST, bool PACKED, int W>
+__device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, const CellGeom &G,
+                             bool valid, int cx, int cy, uint32_t w, double hwin, uint64_t seed,
+                             const uint8_t *src, uint8_t *dst, int lane, uint32_t *ev_out,
+                             bool *amb_out, bool *bad_out)
+{
+    using TR = Traits<MODEL>;
+    static_assert(is_spin_flip<MODEL>(), "grouped cells are built for the spin-flip models");
+    constexpr bool F64 = sizeof(CLK) == 8;
+    constexpr int K = TR::K, HW = TR::HW;
+    constexpr int CPL = (K + W - 1) / W;  // classes per lane: lane l holds classes l, l + W, ...
+    constexpr bool ring = MODEL == ISING1D;
+    constexpr int SK = ring ? 3 : 5;      // class stride of sigma; lanes refreshing one flip
+    static_assert(W >= SK && W < 32, "a group needs a lane per refreshed site");
+    const int gl = lane & (W - 1);
+    const int gshift = lane & ~(W - 1);
+    const uint32_t gbits = (1u << W) - 1u;
+    const int qx = G.qx, qy = G.qy;
+    const int BW = Lo.BW, BH = Lo.BH, nsite = Lo.nsite;
+    const int NL = (nsite + 31) >> 5;  // lanes that own sites (<= W)
+    uint8_t *box = csm;
+    uint8_t *scls = csm + Lo.scls_off;
+    uint32_t *mask = reinterpret_cast<uint32_t *>(csm + Lo.mask_off);
+    int *cnt = reinterpret_cast<int *>(csm + Lo.cnt_off);
+    double *dcnt = reinterpret_cast<double *>(csm + Lo.dcnt_off);
+
+    const int lx = R.lx, ly = R.ly;
+    const int m = cy * R.ncx + cx;
+    const int X0 = cx * qx, Y0 = cy * qy;
+
+    // Stage the cell and its halo (periodic wrap) from the window-start
+    // state; on the ring only the cell's own row.
+    if (valid) {
+        for (int i = gl; i < (ring ? BW : BW * BH); i += W) {
+            const int by = ring ? HW : i / BW, bx = ring ? i : i - by * BW;
+            int gy = Y0 - HW + by, gx = X0 - HW + bx;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+            const int bi = by * BW + bx;
+            if (PACKED) {
+                const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
+                const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
+                box[bi] = (uint8_t)((wv >> (gx & 31)) & 1u);
+            } else {
+                box[bi] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+            }
+        }
+    }
+    for (int i = gl; i < MAX_CLASSES; i += W) cnt[i] = 0;  // a cell-less group keeps zero rates
+    __syncwarp();
+
+    // Class build: lane gl classifies its run of 32 sites (word gl; words
+    // past the cell's last site are zero).
+    if (valid) {
+        uint32_t mk[TR::KS];
+#pragma unroll
+        for (int k = 0; k < TR::KS; ++k) mk[k] = 0u;
+        for (int t = 0; t < 32; ++t) {
+            const int i = gl * 32 + t;
+            if (i >= nsite) break;
+            const int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
+            const int k = site_class<MODEL>(box, BW, (lly + HW) * BW + llx + HW);
+            scls[i] = (uint8_t)k;
+#pragma unroll
+            for (int kk = 0; kk < TR::KS; ++kk) mk[kk] |= (uint32_t)(k == kk) << t;
+        }
+#pragma unroll
+        for (int k = 0; k < TR::KS; ++k) mask[k * W + gl] = mk[k];
+    }
+    __syncwarp();
+    if (valid) {
+#pragma unroll
+        for (int s = 0; s < CPL; ++s) {
+            const int k = gl + W * s;
+            if (k < K) {
+                int c = 0;
+                for (int l = 0; l < NL; ++l) c += __popc(mask[k * W + l]);
+                cnt[k] = c;
+            }
+        }
+    }
+    __syncwarp();
+
+    double rk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) rk[k] = F64 ? R.r[k] : 0.0;
+    uint64_t rq[CPL];
+#pragma unroll
+    for (int s = 0; s < CPL; ++s) {
+        const int k = gl + W * s;
+        rq[s] = (!F64 && k < K) ? R.rq[k] : 0ull;
+    }
+    const float qscale = R.qscale;
+    const long long hbits = dbits(hwin);
+    const float hf = (float)hwin;
+    double tau = 0.0;
+    float tauf = 0.0f;
+    bool act = valid, amb = false, bad = false;
+    uint32_t ev = 0;
+    uint32_t rw2 = 0, rw3 = 0;
+    double rl = 0.0, ruc = 0.0;
+    float rlf = 0.0f;
+    const uint32_t ctr3 = R.rep | (TAG_EVENT << 24);
+
+    // Every running group executes event e in iteration e, so e is the same
+    // for all of them and the draw batches stay aligned.
+    for (uint32_t e = 0;; ++e) {
+        if (!__any_sync(FULL, act)) break;
+        double Pd[K];
+        double lamd = 0.0;
+        uint64_t P[CPL];
+        uint64_t lami = 0;
+        if (F64) {
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                const int k = gl + W * s;
+                if (k < K) dcnt[k] = small_to_double(cnt[k]);  // one conversion per class, lane-parallel
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                lamd = __fma_rn(dcnt[k], rk[k], lamd);  // fma(0, r, x) == x
+                Pd[k] = lamd;
+            }
+            if (dbits(lamd) == 0) act = false;
+        } else {
+            // exact integer prefix sums in class order: a width-W scan per
+            // class slot, then the slots' running bases
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                const int k = gl + W * s;
+                P[s] = (uint64_t)(k < K ? (uint32_t)cnt[k] : 0u) * rq[s];
+#pragma unroll
+                for (int off = 1; off < W; off <<= 1) {
+                    const uint64_t v = __shfl_up_sync(FULL, P[s], off, W);
+                    if (gl >= off) P[s] += v;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < CPL; ++s) {
+                const uint64_t tot = __shfl_sync(FULL, P[s], W - 1, W);
+                P[s] += lami;
+                lami += tot;
+            }
+            if (lami == 0ull) act = false;
+        }
+        if (e >= MAX_EVENTS_PER_WINDOW) {  // cannot happen with sane rates; never loop unboundedly
+            bad = bad || act;
+            act = false;
+        }
+        if ((e & (uint32_t)(W - 1)) == 0u) {
+            // W events' draws at once, one Philox block per lane
+            const u32x4 o = draw(seed, e + (uint32_t)gl, w, (uint32_t)m, ctr3);
+            if (F64) {
+                const uint64_t b = ((uint64_t)o.x << 21) | (uint64_t)(o.y >> 11);
+                rl = neg_log_u53(b + 1ull);
+                ruc = u53_scaled(2ull * o.z + 1ull, 33);  // (o.z + 1/2) 2^-32
+            } else {
+                rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
+            }
+            rw2 = o.z;
+            rw3 = o.w;
+        }
+        const int sl = (int)(e & (uint32_t)(W - 1));
+        const uint32_t w3 = __shfl_sync(FULL, rw3, sl, W);
+        int k;
+        if (F64) {
+            const double l = __shfl_sync(FULL, rl, sl, W);
+            const double uc = __shfl_sync(FULL, ruc, sl, W);
+            const double end = __dadd_rn(tau, div_rn(l, lamd));
+            const long long eb = dbits(end);
+            if (act && llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+            if (eb >= hbits) act = false;
+            if (act) tau = end;
+            const long long tb = dbits(__dmul_rn(uc, lamd));
+            k = K - 1;
+#pragma unroll
+            for (int kk = K - 2; kk >= 0; --kk)
+                if (tb < dbits(Pd[kk])) k = kk;
+        } else {
+            const float l = __shfl_sync(FULL, rlf, sl, W);
+            const uint32_t w2 = __shfl_sync(FULL, rw2, sl, W);
+            const float lamf = lami ? __fmul_rn(u64_to_float_rz(lami), qscale) : 0.0f;
+            const float end = __fadd_rn(tauf, __fdividef(l, lamf));
+            if (end >= hf) act = false;
+            if (act) tauf = end;
+            const uint64_t t = (uint64_t)w2 * (lami >> 32) + (((uint64_t)w2 * (lami & 0xffffffffull)) >> 32);
+            k = -1;
+#pragma unroll
+            for (int s = CPL - 1; s >= 0; --s) {
+                const bool in = gl + W * s < K && t < P[s];
+                const uint32_t b = (__ballot_sync(FULL, in) >> gshift) & gbits;
+                if (b) k = W * s + __ffs(b) - 1;
+            }
+            if (k < 0) k = 0;  // only in a group whose window has ended
+        }
+        const int nk = cnt[k];
+        const uint32_t j = (uint32_t)(((uint64_t)w3 * (uint64_t)(uint32_t)nk) >> 32);
+
+        // Rank search: the j-th member of class k in canonical order.
+        const uint32_t mw = gl < NL ? mask[k * W + gl] : 0u;
+        const int c = __popc(mw);
+        int incl = c;
+#pragma unroll
+        for (int off = 1; off < W; off <<= 1) {
+            if (off < NL) {
+                const int v = __shfl_up_sync(FULL, incl, off, W);
+                if (gl >= off) incl += v;
+            }
+        }
+        const uint32_t hit = (__ballot_sync(FULL, (uint32_t)incl > j) >> gshift) & gbits;
+        if (act && hit == 0u) {  // counts and masks disagree: stop rather than write out of bounds
+            bad = true;
+            act = false;
+        }
+        const int owner = hit ? __ffs(hit) - 1 : 0;
+        int pick = 0;
+        if (gl == owner) pick = select_bit(mw, (int)j - (incl - c));
+        pick = __shfl_sync(FULL, pick, owner, W);
+
+        // Spin flip at the picked site: its class k = SK sigma + n becomes
+        // k -+ SK, and each neighbour inside the cell changes n by +-1 (lanes
+        // 1..4: N, E, S, W; on the ring lanes 1, 2: x + 1, x - 1).
+        if (act) {
+            const int site = owner * 32 + pick;
+            const int sy = (int)fdiv((uint32_t)site, G.fqx), sx = site - sy * qx;
+            const int sold = k >= SK;
+            if (gl == 0) box[(sy + HW) * BW + sx + HW] = (uint8_t)(1 - sold);
+            if (gl < SK) {
+                int ux = sx, uy = sy;
+                if (ring) { ux += gl == 1 ? 1 : (gl == 2 ? -1 : 0); }
+                else if (gl > 0) { ux += dir_dx(gl - 1); uy += dir_dy(gl - 1); }
+                if (ux >= 0 && ux < qx && uy >= 0 && uy < qy) {
+                    const int i = uy * qx + ux;
+                    int kold, knew;
+                    if (gl == 0) { kold = k; knew = sold ? k - SK : k + SK; }
+                    else { kold = (int8_t)scls[i]; knew = kold + (sold ? -1 : 1); }
+                    scls[i] = (uint8_t)knew;
+                    const int own = i >> 5;
+                    const uint32_t bit = 1u << (i & 31);
+                    atomicXor(&mask[kold * W + own], bit);
+                    atomicXor(&mask[knew * W + own], bit);
+                    atomicSub(&cnt[kold], 1);
+                    atomicAdd(&cnt[knew], 1);
+                }
+            }
+            ++ev;
+        }
+        __syncwarp();
+    }
+
+    // Write back the cell (a word shared with a neighbouring cell is updated
+    // with atomics on this cell's bits only).
+    if (valid) {
+        if (PACKED) {
+            uint32_t *dst32 = reinterpret_cast<uint32_t *>(dst);
+            const int wa = X0 >> 5, nwr = ((X0 + qx - 1) >> 5) - wa + 1;
+            for (int t = gl; t < qy * nwr; t += W) {
+                const int row = t / nwr, wi = wa + (t - row * nwr);
+                const uint8_t *brow = box + (row + HW) * BW + HW - X0;
+                uint32_t *drow = dst32 + (int64_t)(Y0 + row) * (lx >> 5);
+                const int xs = max(X0, wi << 5), xe = min(X0 + qx, (wi + 1) << 5);
+                uint32_t msk = 0u, bits = 0u;
+                for (int xx = xs; xx < xe; ++xx) {
+                    const uint32_t b = 1u << (xx & 31);
+                    msk |= b;
+                    if (brow[xx]) bits |= b;
+                }
+                if (msk == 0xffffffffu) {
+                    drow[wi] = bits;
+                } else {
+                    atomicAnd(drow + wi, ~msk);
+                    atomicOr(drow + wi, bits);
+                }
+            }
+        } else {
+            for (int i = gl; i < nsite; i += W) {
+                const int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
+                dst[(int64_t)(Y0 + lly) * lx + X0 + llx] = box[(lly + HW) * BW + llx + HW];
+            }
+        }
+    }
+    *ev_out = ev;
+    *amb_out = amb;
+    *bad_out = bad;
+}
+
+// Totals of a warp's groups: events, ambiguous and failed cell-windows (one
+// atomic each per warp).
+template <int W>
+__device__ __forceinline__ void add_counters(unsigned long long *counters, int lane, bool valid,
+                                             uint32_t ev, bool amb, bool bad)
+{
+    const bool lead = valid && (lane & (W - 1)) == 0;
+    const uint32_t tot = __reduce_add_sync(FULL, lead ? ev : 0u);
+    const int na = __popc(__ballot_sync(FULL, lead && amb));
+    const int nb = __popc(__ballot_sync(FULL, lead && bad));
+    if (lane == 0) {
+        atomicAdd(&counters[0], (unsigned long long)tot);
+        if (na) atomicAdd(&counters[1], (unsigned long long)na);
+        if (nb) atomicAdd(&counters[3], (unsigned long long)nb);
+    }
+}
+
+// Plain engine: one launch per window; warp u runs active cells GC u ..
+// GC u + GC - 1 of one replica (GC = 32/W cells per warp).
+template <int MODEL, typename CLK, bool PACKED, int W>
+__global__ void __launch_bounds__(256) fs_group_kernel(WindowArgs a, int nactive, int stride)
+{
+    constexpr int GC = 32 / W;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (warp * GC >= nactive) return;  // the whole warp
+    const int cell = warp * GC + lane / W;
+    const bool valid = cell < nactive;
+    const Replica &R = a.reps[a.rep_index];
+    int cx = 0, cy = 0;
+    if (valid) {
+        if (a.order) {  // heaviest-first issue list
+            const int mo = a.order[cell];
+            cy = mo / R.ncx;
+            cx = mo - cy * R.ncx;
+        } else {
+            const int half = R.ncx >> 1;
+            cy = cell / half;
+            cx = 2 * (cell % half) + ((a.colour + cy) & 1);
+        }
+    }
+    const GLayout Lo = make_glayout<MODEL>(a.geom.qx, a.geom.qy, W);
+    uint8_t *csm = smem + (size_t)(wib * GC + lane / W) * stride;
+    uint32_t ev;
+    bool amb, bad;
+    group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cx, cy, a.w, a.h, a.seed,
+                                                a.src + R.lat_off, a.dst + R.lat_off, lane, &ev,
+                                                &amb, &bad);
+    if (valid && (lane & (W - 1)) == 0) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)ev;
+    add_counters<W>(a.counters, lane, valid, ev, amb, bad);
+}
+
+// Persistent engine (in-place spin-flip models): a task is a chunk of GC
+// consecutive active cells of one window (they never depend on each other);
+// chunks are dequeued window-major, so a chunk waits only on chunks of
+// earlier windows, which running warps hold or have finished. Each group
+// waits for its own cell's dependencies -- its previous active window and
+// its edge neighbours' last active window before this one (epoch = 1 + last
+// active window) -- with the bounded, backed-off polls of wait_epochs.
+template <int MODEL, typename CLK, bool PACKED, int W>
+__global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams *pp, int stride)
+{
+    constexpr int GC = 32 / W;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const PParams &P = *pp;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int gl = lane & (W - 1);
+    uint8_t *csm = smem + (size_t)(wib * GC + lane / W) * stride;
+    const GLayout Lo = make_glayout<MODEL>(P.geom.qx, P.geom.qy, W);
+    const int per_window = P.total_active;
+    const int chunks = (per_window + GC - 1) / GC;
+    const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)chunks;
+
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(P.queue, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= total) break;
+        int ab = 0;
+        if (lane == 0) ab = *(volatile int32_t *)P.abort_flag;
+        if (__shfl_sync(FULL, ab, 0)) break;
+        const int i = (int)(t / (unsigned long long)chunks);
+        const int ch = (int)(t % (unsigned long long)chunks);
+        const int u = ch * GC + lane / W;
+        const bool valid = u < per_window;
+        const int a = valid ? u : ch * GC;  // a cell-less group borrows the chunk's first cell's replica
+        int lo = 0, hi = P.nrep;            // last r with act_prefix[r] <= a
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (P.act_prefix[mid] <= a) lo = mid; else hi = mid;
+        }
+        const int r = lo;
+        const int k = a - P.act_prefix[r];
+        const Replica &R = P.reps[r];
+        const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
+        const int ccol = P.colour[widx];
+        int cx, cy;
+        if (P.order) {
+            const int mo = P.order[R.cell_off + ccol * ((R.ncx >> 1) * R.ncy) + k];
+            cy = mo / R.ncx;
+            cx = mo - cy * R.ncx;
+        } else {
+            const int half = R.ncx >> 1;
+            cy = k / half;
+            cx = 2 * (k % half) + ((ccol + cy) & 1);
+        }
+        const int m = cy * R.ncx + cx;
+        int32_t *ep = P.epoch + R.cell_off;
+        uint8_t *cur = P.lat + R.lat_off;
+
+        // Dependency 0: the cell's previous active window; 1..4: the edge
+        // neighbours' (E, S, W, N) last active window before this one. A ring
+        // (one row of cells) has no vertical neighbours. Lane gl of a group
+        // waits on dependencies gl, gl + W.
+        const int2 pv = P.prev[widx];
+        bool ok = true;
+#pragma unroll
+        for (int d0 = 0; d0 < 5; d0 += W) {
+            const int d = d0 + gl;
+            const int ex = d == 1 ? 1 : (d == 3 ? -1 : 0);
+            const int ey = d == 2 ? 1 : (d == 4 ? -1 : 0);
+            const int dcx = (cx + ex + R.ncx) % R.ncx, dcy = (cy + ey + R.ncy) % R.ncy;
+            const int target = (d == 0 ? pv.x : pv.y) + 1;
+            const bool dep = valid && d < 5 && target > 0 && !(ey != 0 && R.ncy == 1);
+            if (ok) ok = wait_epochs(ep, dcy * R.ncx + dcx, dep, target, P, lane);  // warp-uniform
+        }
+        if (!ok) break;
+
+        uint32_t ev;
+        bool amb, bad;
+        group_window<MODEL, CLK, true, PACKED, W>(csm, Lo, R, P.geom, valid, cx, cy, P.w0 + (uint32_t)i,
+                                                   P.h[i], P.seed, cur, cur, lane, &ev, &amb, &bad);
+        if (valid && gl == 0) P.workload[R.cell_off + m] = (int32_t)ev;
+        add_counters<W>(P.counters, lane, valid, ev, amb, bad);
+        __syncwarp();
+        if (valid && gl == 0) {
+            __threadfence();
+            cuda::atomic_ref<int32_t, cuda::thread_scope_device> ea(ep[m]);
+            ea.store(i + 1, cuda::memory_order_release);
+        }
+    }
+}
+
+}  // namespace
+
+}  // namespace fskmc

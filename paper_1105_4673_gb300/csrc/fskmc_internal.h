@@ -68,10 +68,32 @@ struct WindowArgs {
     unsigned long long *counters;  // [0] events, [1] ambiguous cell-windows, [2] timeouts
     int32_t packed;            // lattice stored 1 bit per site (spin-flip models)
     const int32_t *order;      // active cells of the window (cell ids) in issue order, or null
+    int32_t lanes_per_cell;    // 32: one cell per warp; 4, 8 or 16: grouped (spin-flip models)
 };
 
 // Shared-memory bytes one warp of the window kernel needs.
 size_t window_smem_per_warp(int model, int qx, int qy);
+// Warps of the one-cell window kernel that fit on the device at once with
+// wpb warps per block (0 if unknown).
+int window_resident_warps(int model, int fp32, bool packed, int qx, int qy, int wpb);
+
+// Lanes per cell of the grouped window kernels (several small cells per
+// warp, spin-flip models only): the lanes owning the cell's 32-site words,
+// rounded up to a power of two and at least the lanes one flip's class
+// refresh uses (8 in 2D, 4 on a ring); 32 means the cell takes a whole warp
+// (not grouped).
+int group_width(int model, int qx, int qy);
+// Shared-memory bytes one warp of the grouped kernels needs (0 if not grouped).
+size_t group_smem_per_warp(int model, int qx, int qy);
+// The grouped kernel for (model, clock, storage, cell shape): plain window
+// kernel (args: WindowArgs, int nactive, int stride) or persistent kernel
+// (args: const PParams *, int stride), stride = group_smem_per_warp / (32 / W).
+void *group_kernel_for(int model, int fp32, bool packed, int qx, int qy, bool persistent);
+// The same per clock, for W lanes per cell.
+void *group_kernel_f64(int model, bool packed, int lanes, bool persistent);
+void *group_kernel_f32(int model, bool packed, int lanes, bool persistent);
+cudaError_t launch_group_window(int model, int fp32, const WindowArgs &a, int nactive, int wpb,
+                                cudaStream_t s);
 
 // Launch one window (all active cells of a.rep_index).
 cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int ncells_active,
@@ -109,6 +131,9 @@ cudaError_t launch_order(const Replica *reps_host, const Replica *reps_dev, int 
 // hardware correctly rounded divide: counts disagreeing pairs into *bad.
 cudaError_t launch_div_selftest(const double *a, const double *b, int n, unsigned int *bad,
                                 cudaStream_t s);
+
+// The window kernels' binary64 -log(n 2^-53) for n[i] in [1, 2^53] into out.
+cudaError_t launch_log_selftest(const unsigned long long *n, int count, double *out, cudaStream_t s);
 
 // Validation of a lattice: counts bytes >= nstates into *bad.
 cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned int *bad,

@@ -28,6 +28,7 @@ struct PersistentRun {
     bool packed;                  // bit-packed lattice (spin-flip models)
     const int32_t *order;         // device: active cells per replica and colour, heaviest
                                   // first (see launch_order), or null for row-major order
+    int lanes_per_cell;           // 32, or the width of the grouped kernel (spin-flip models)
 };
 
 struct PersistentState;  // device buffers and the captured CUDA graph

@@ -24,164 +24,12 @@
 #include <string>
 #include <vector>
 
+#include "fskmc_device.cuh"
 #include "fskmc_internal.h"
 #include "fskmc_persistent.h"
 #include "philox.cuh"
 
 namespace fskmc {
-
-namespace {
-
-constexpr uint32_t MAX_EVENTS_PER_WINDOW = 1u << 26;
-
-template <int MODEL>
-struct Traits;
-// K classes; KS site classes and KB slot classes with their own masks;
-// HW halo width; R radius (in sites) within which an event can change a
-// member's class.
-template <> struct Traits<ADSDES> { static constexpr int K = 10, KS = 10, KB = 0, HW = 1, R = 1; };
-template <> struct Traits<ISING> { static constexpr int K = 10, KS = 10, KB = 0, HW = 1, R = 1; };
-template <> struct Traits<DIFFUSION> { static constexpr int K = 15, KS = 10, KB = 5, HW = 2, R = 2; };
-template <> struct Traits<ZGB> { static constexpr int K = 4, KS = 2, KB = 2, HW = 1, R = 1; };
-template <> struct Traits<ISING1D> { static constexpr int K = 6, KS = 6, KB = 0, HW = 1, R = 1; };
-
-// Spin-flip models: class = SPIN_STRIDE * sigma + n, n = occupied neighbours.
-template <int MODEL>
-constexpr bool is_spin_flip() { return MODEL == ADSDES || MODEL == ISING || MODEL == ISING1D; }
-
-__device__ __forceinline__ int dir_dx(int d) { return d == 1 ? 1 : (d == 3 ? -1 : 0); }
-__device__ __forceinline__ int dir_dy(int d) { return d == 0 ? -1 : (d == 2 ? 1 : 0); }
-
-// Is class k a slot (two-site) class, and which mask holds it.
-template <int MODEL>
-__device__ __forceinline__ bool is_slot(int k)
-{
-    if (MODEL == DIFFUSION) return k >= 10;
-    if (MODEL == ZGB) return k == 1 || k == 2;
-    return false;
-}
-template <int MODEL>
-__device__ __forceinline__ int mask_of(int k)
-{
-    if (MODEL == DIFFUSION) return k >= 10 ? k - 10 : k;
-    if (MODEL == ZGB) return k == 0 ? 0 : (k == 3 ? 1 : k - 1);
-    return k;
-}
-template <int MODEL>
-__device__ __forceinline__ int slot_class_of_mask(int mb)
-{
-    return MODEL == DIFFUSION ? 10 + mb : 1 + mb;
-}
-
-// Box = the cell plus a halo of HW sites, row stride BW.
-template <int MODEL>
-__device__ __forceinline__ int occ4(const uint8_t *box, int BW, int p)
-{
-    return (box[p - BW] == 1) + (box[p + 1] == 1) + (box[p + BW] == 1) + (box[p - 1] == 1);
-}
-
-template <int MODEL>
-__device__ __forceinline__ int site_class(const uint8_t *box, int BW, int p)
-{
-    int s = box[p];
-    if (MODEL == ZGB) return s == 0 ? 0 : (s == 1 ? 3 : -1);
-    if (MODEL == ISING1D) return 3 * s + (box[p - 1] == 1) + (box[p + 1] == 1);  // ring: x -+ 1
-    return 5 * s + occ4<MODEL>(box, BW, p);
-}
-
-template <int MODEL>
-__device__ __forceinline__ int slot_class(const uint8_t *box, int BW, int po, int pt)
-{
-    int so = box[po], st = box[pt];
-    if (MODEL == DIFFUSION) return (so == 1 && st == 0) ? 10 + occ4<MODEL>(box, BW, po) : -1;
-    if (MODEL == ZGB) {
-        if (so == 0 && st == 0) return 1;
-        if ((so == 1 && st == 2) || (so == 2 && st == 1)) return 2;
-        return -1;
-    }
-    return -1;
-}
-
-// Does a cell of colour col own slot d (0..3 outward, 4..7 inward) of local
-// site (lx, ly)? Bonds inside the cell belong to it; a horizontal bond across
-// a cell edge belongs to the E cell, a vertical one to the O cell.
-__device__ __forceinline__ bool slot_owned(int lx, int ly, int d, int qx, int qy, int col)
-{
-    int dir = d & 3;
-    int nlx = lx + dir_dx(dir), nly = ly + dir_dy(dir);
-    bool inside = nlx >= 0 && nlx < qx && nly >= 0 && nly < qy;
-    bool cross = (dir & 1) ? (col == 0) : (col == 1);
-    return (d >= 4) ? (!inside && cross) : (inside || cross);
-}
-
-// Position of the r-th (0-based) set bit of m (r < popc(m)).
-__device__ __forceinline__ int select_bit(uint32_t m, int r)
-{
-    int pos = 0, c;
-    c = __popc(m & 0xFFFFu); if (r >= c) { r -= c; m >>= 16; pos += 16; }
-    c = __popc(m & 0xFFu);   if (r >= c) { r -= c; m >>= 8;  pos += 8; }
-    c = __popc(m & 0xFu);    if (r >= c) { r -= c; m >>= 4;  pos += 4; }
-    c = __popc(m & 0x3u);    if (r >= c) { r -= c; m >>= 2;  pos += 2; }
-    c = (int)(m & 1u);       if (r >= c) { pos += 1; }
-    return pos;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f)
-{
-    return (uint32_t)(((uint64_t)n * f.M) >> 32);
-}
-
-// Bit pattern of a non-negative double: orders like the value.
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-
-// x (0 < x < 2^63) as a binary32 with its significand truncated to 24 bits,
-// built on the integer pipes (the 64-bit conversion instruction runs on the
-// FP64 pipe).
-__device__ __forceinline__ float u64_to_float_rz(uint64_t x)
-{
-    const int lz = __clzll((long long)x);
-    const uint32_t m = (uint32_t)((x << lz) >> 40);
-    return __uint_as_float(((uint32_t)(190 - lz) << 23) | (m & 0x7FFFFFu));
-}
-
-}  // namespace
-
-// a / b rounded to nearest (ties to even) for a >= 0 and b > 0, computed on
-// the integer pipes: with 53-bit significands ma, mb the quotient
-// significand is Q = floor(ma 2^s / mb) in [2^52, 2^53) (s = 52 or 53) and
-// the exact remainder R = ma 2^s - Q mb decides the rounding (2R vs mb). On
-// GB300 the FP64 pipe is the window kernel's bottleneck; this keeps the
-// divide off it. Cases whose result would not be a normal number (or whose
-// divisor is subnormal) go to the hardware divide.
-__device__ double div_rn(double a, double b)
-{
-    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
-    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
-    if (A == 0ull) return 0.0;
-    const long long ea = (long long)(A >> 52), eb = (long long)(B >> 52);
-    if (ea == 0 || eb == 0 || ea == 2047 || eb == 2047) return __ddiv_rn(a, b);
-    const unsigned long long FRAC = (1ull << 52) - 1ull;
-    const unsigned long long ma = (A & FRAC) | (1ull << 52), mb = (B & FRAC) | (1ull << 52);
-    long long e = ea - eb + 1023;
-    unsigned __int128 N;
-    if (ma >= mb) {
-        N = (unsigned __int128)ma << 52;
-    } else {
-        N = (unsigned __int128)ma << 53;
-        e -= 1;
-    }
-    if (e < 1 || e > 2045) return __ddiv_rn(a, b);
-    unsigned long long Q = (unsigned long long)(N / mb);
-    const unsigned long long R = (unsigned long long)(N - (unsigned __int128)Q * mb);
-    if (2ull * R > mb || (2ull * R == mb && (Q & 1ull))) {
-        Q += 1ull;
-        if (Q == (1ull << 53)) {
-            Q >>= 1;
-            e += 1;
-        }
-    }
-    return __longlong_as_double((long long)(((unsigned long long)e << 52) | (Q & FRAC)));
-}
 
 namespace {
 
@@ -259,15 +107,6 @@ __host__ __device__ inline Layout make_layout(int qx, int qy)
               4 * MAX_CLASSES + 8 * MAX_CLASSES + 8 * MAX_CLASSES + 4 * L.rowmask_words;
     L.bytes = (L.bytes + 15) & ~15;
     return L;
-}
-
-// Global-memory access for staging: through L2 only in the persistent
-// kernel, whose cells read sites that other SMs wrote within the same launch.
-template <bool PERSIST>
-__device__ __forceinline__ uint8_t ld_site(const uint8_t *p)
-{
-    if (PERSIST) return __ldcg(p);
-    return *p;
 }
 
 // Copy the sites of inactive cell (cx, cy) that no active cell writes in a
@@ -598,8 +437,8 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             u32x4 o = draw(seed, e + (uint32_t)lane, w, (uint32_t)m, ctr3);
             if (F64) {
                 uint64_t b = ((uint64_t)o.x << 21) | (uint64_t)(o.y >> 11);
-                rl = -log(__dmul_rn(__ull2double_rn(b + 1ull), 0x1p-53));
-                ruc = __dmul_rn(__dadd_rn(__uint2double_rn(o.z), 0.5), 0x1p-32);
+                rl = neg_log_u53(b + 1ull);
+                ruc = u53_scaled(2ull * o.z + 1ull, 33);  // (o.z + 1/2) 2^-32
             } else {
                 rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
             }
@@ -906,62 +745,6 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
 // Every wait polls at most spin_limit times; on expiry the warp raises the
 // abort flag, counts a timeout and the whole launch drains.
 // ---------------------------------------------------------------------------
-struct PParams {
-    const Replica *reps;
-    int32_t nrep;
-    CellGeom geom;
-    uint8_t *lat, *lat2;
-    int32_t *workload;
-    unsigned long long *counters;
-    const int32_t *act_prefix;  // [nrep + 1] prefix sums of active cells per window
-    int32_t total_cells, total_active;
-    const int8_t *colour;
-    int32_t colour_per_replica;
-    const int2 *prev;          // per (replica,) window: last earlier window of the same / other colour
-    const int32_t *order;      // per replica and colour: active cells heaviest first, or null
-    int32_t inplace;           // in-place models: only active cells have tasks
-    const double *h;
-    int64_t nwin;
-    uint32_t w0;
-    uint64_t seed;
-    uint32_t spin_limit;
-    int32_t *epoch;
-    unsigned long long *queue;
-    int32_t *abort_flag;
-};
-
-// Lanes with has_dep poll ep[dep] until it reaches their target. Polls are
-// relaxed loads with exponential back-off (128 ns doubling to 4 us), so
-// waiting warps leave the issue slots to working ones; one acquire fence
-// after success orders the cell's later reads. Returns false on timeout
-// (after P.spin_limit polls) or when another warp raised the abort flag.
-__device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target,
-                            const PParams &P, int lane)
-{
-    uint32_t spins = 0;
-    unsigned ns = 128;
-    for (;;) {
-        bool ok = !has_dep || *(volatile const int32_t *)(ep + dep) >= target;
-        if (__all_sync(0xffffffffu, ok)) break;
-        if (spins >= P.spin_limit) {
-            if (lane == 0) {
-                atomicExch(P.abort_flag, 1);
-                atomicAdd(&P.counters[2], 1ull);
-            }
-            return false;
-        }
-        ++spins;
-        if ((spins & 15u) == 0u) {
-            int ab = *(volatile int32_t *)P.abort_flag;
-            if (__any_sync(0xffffffffu, ab != 0)) return false;
-        }
-        __nanosleep(ns);
-        if ((spins & 3u) == 0u && ns < 4096u) ns <<= 1;
-    }
-    __threadfence();
-    __syncwarp();
-    return true;
-}
 
 template <int MODEL, typename CLK, bool PACKED>
 __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, int smem_per_warp)
@@ -1071,6 +854,7 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
 template <int MODEL>
 cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
 {
+    if (a.lanes_per_cell < 32) return launch_group_window(MODEL, fp32, a, nactive, wpb, st);
     const int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
     size_t smem = (size_t)spw * wpb;
     int blocks = (nactive + wpb - 1) / wpb;
@@ -1083,6 +867,17 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
     return cudaGetLastError();
+}
+
+template <int MODEL>
+void *window_kernel_ptr(int fp32, bool packed)
+{
+    if constexpr (is_spin_flip<MODEL>()) {
+        if (packed)
+            return fp32 ? (void *)fs_window_kernel<MODEL, float, true>
+                        : (void *)fs_window_kernel<MODEL, double, true>;
+    }
+    return fp32 ? (void *)fs_window_kernel<MODEL, float, false> : (void *)fs_window_kernel<MODEL, double, false>;
 }
 
 template <int MODEL>
@@ -1110,6 +905,29 @@ void *persistent_kernel_for(int model, int fp32, bool packed)
 }
 
 }  // namespace
+
+int window_resident_warps(int model, int fp32, bool packed, int qx, int qy, int wpb)
+{
+    void *kern = nullptr;
+    switch (model) {
+    case ADSDES: kern = window_kernel_ptr<ADSDES>(fp32, packed); break;
+    case ISING: kern = window_kernel_ptr<ISING>(fp32, packed); break;
+    case DIFFUSION: kern = window_kernel_ptr<DIFFUSION>(fp32, false); break;
+    case ZGB: kern = window_kernel_ptr<ZGB>(fp32, false); break;
+    case ISING1D: kern = window_kernel_ptr<ISING1D>(fp32, packed); break;
+    }
+    const size_t smem = window_smem_per_warp(model, qx, qy) * (size_t)wpb;
+    int per_sm = 0, dev = 0, nsm = 0;
+    if (!kern || smem > 200 * 1024) return 0;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return per_sm * wpb * nsm;
+}
 
 size_t window_smem_per_warp(int model, int qx, int qy)
 {
@@ -1139,7 +957,7 @@ cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int nactive,
 // Device buffers of the persistent engine and the graph that launches it:
 // reset the per-cell epochs and the queue, then run the persistent kernel.
 struct PersistentState {
-    int model = -1, fp32 = -1, wpb = -1, grid = 0, packed = -1;
+    int model = -1, fp32 = -1, wpb = -1, grid = 0, packed = -1, lanes = -1;
     PParams *d_params = nullptr;
     int32_t *d_epoch = nullptr;
     unsigned long long *d_queue = nullptr;  // [0] queue, [1] abort flag (low word)
@@ -1200,12 +1018,19 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     }
     // (Re)build the graph when the kernel variant or launch shape changes.
     if (st->model != run.model || st->fp32 != run.fp32 || st->wpb != run.wpb ||
-        st->packed != (int)run.packed) {
+        st->packed != (int)run.packed || st->lanes != run.lanes_per_cell) {
         if (st->exec) { cudaGraphExecDestroy(st->exec); st->exec = nullptr; }
         if (st->graph) { cudaGraphDestroy(st->graph); st->graph = nullptr; }
-        void *kern = persistent_kernel_for(run.model, run.fp32, run.packed);
-        const int spw = (int)window_smem_per_warp(run.model, run.qx, run.qy);
-        const size_t smem = (size_t)spw * run.wpb;
+        // grouped kernel (several cells per warp) or one cell per warp; the
+        // kernel's int argument is the per-cell or per-warp shared memory
+        const bool grouped = run.lanes_per_cell < 32;
+        void *kern = grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
+                             : persistent_kernel_for(run.model, run.fp32, run.packed);
+        if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
+        const int wbytes = grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
+                                   : (int)window_smem_per_warp(run.model, run.qx, run.qy);
+        const int spw = grouped ? wbytes / (32 / run.lanes_per_cell) : wbytes;
+        const size_t smem = (size_t)wbytes * run.wpb;
         PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0, dev = 0, nsm = 0;
         PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * run.wpb, smem));
@@ -1229,6 +1054,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         st->fp32 = run.fp32;
         st->wpb = run.wpb;
         st->packed = (int)run.packed;
+        st->lanes = run.lanes_per_cell;
     }
     const size_t ncol = (size_t)run.nwin * (run.colour_per_replica ? run.nrep : 1);
     if (ncol > st->colour_cap) {
@@ -1299,9 +1125,26 @@ __global__ void div_selftest_kernel(const double *a, const double *b, int n, uns
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const double x = div_rn(a[i], b[i]), y = __ddiv_rn(a[i], b[i]);
+        const double y = __ddiv_rn(a[i], b[i]);
+        const double x = div_rn(a[i], b[i]);
+        bool slow;
+        double z = div_newton(a[i], b[i], slow);
+        if (slow) z = y;  // the caller's fallback
         if (__double_as_longlong(x) != __double_as_longlong(y)) atomicAdd(bad, 1u);
+        if (__double_as_longlong(z) != __double_as_longlong(y)) atomicAdd(bad, 1u);
     }
+}
+
+__global__ void log_selftest_kernel(const unsigned long long *nn, int n, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = neg_log_u53(nn[i]);
+}
+
+cudaError_t launch_log_selftest(const unsigned long long *nn, int n, double *out, cudaStream_t s)
+{
+    if (n > 0) log_selftest_kernel<<<(n + 255) / 256, 256, 0, s>>>(nn, n, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_div_selftest(const double *a, const double *b, int n, unsigned int *bad,

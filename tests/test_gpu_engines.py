@@ -192,3 +192,21 @@ def test_integer_divide_matches_hardware():
     a[400:600] = np.nextafter(b[400:600], 0)
     a[600:800] = np.nextafter(b[600:800], np.inf)
     assert F.selftest_divide(a, b) == 0
+
+
+def test_device_log_matches_host_log():
+    """The window clock's table-driven binary64 -log(u_t), u_t = n 2^-53, agrees
+    with the host logarithm to one unit in the last place and equals it for
+    almost every draw; u_t = 1 gives 0."""
+    rng = np.random.default_rng(11)
+    n = rng.integers(1, 2 ** 53, size=1 << 20, dtype=np.uint64, endpoint=True)
+    edges = np.array([1, 2, 3, 2 ** 52, 2 ** 52 + 1, 3 * 2 ** 51 - 1, 3 * 2 ** 51, 2 ** 53 - 1, 2 ** 53],
+                     dtype=np.uint64)
+    n = np.concatenate([edges, n, (2 ** 53 - rng.integers(0, 2 ** 20, size=4096)).astype(np.uint64)])
+    got = F.selftest_log(n)
+    ref = -np.log(n.astype(np.float64) * 2.0 ** -53)
+    assert got[8] == 0.0 and ref[8] == 0.0
+    nz = ref != 0
+    ulps = np.abs(got[nz] - ref[nz]) / np.spacing(np.abs(ref[nz]))
+    assert ulps.max() <= 1.0, ulps.max()
+    assert (got == ref).mean() > 0.99

@@ -1,0 +1,166 @@
+"""Grouped window kernels (several small spin-flip cells per warp, in
+lockstep): bit-identical to one cell per warp and to the oracle, for both
+engines, both clocks and both storages, with partly filled warps, cells of
+every grouped width and cells whose event counts differ widely within a
+warp."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1105_4673_gb300 as F
+from gpu_util import gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+RATES = {
+    "ADSDES": dict(ka=1.0, kd=1.0, betaJ=1.0),
+    "ISING": dict(ka=1.0, kd=1.0, betaJ=0.4407),
+    "ISING1D": dict(ka=1.0, kd=1.0, betaJ=2.0, betah=2.0),
+}
+
+# (model, lx, ly, q, lanes per cell): active cells not a multiple of the
+# cells per warp in most rows
+GEOMS = [
+    ("ISING", 12, 12, (2, 2), 8),       # 18 active cells: 4 full warps + 2 cells
+    ("ISING", 96, 48, (16, 8), 8),      # 18 active 128-site cells
+    ("ISING", 96, 64, (16, 16), 8),     # the benchmark's cell shape
+    ("ADSDES", 128, 64, (32, 16), 16),  # 512-site cells: 2 per warp
+    ("ADSDES", 60, 40, (6, 5), 8),      # ragged cells
+    ("ISING1D", 576, 1, (32, 1), 4),    # 9 active ring cells: 8 per warp + 1
+    ("ISING1D", 1000, 1, (100, 1), 4),
+    ("ISING1D", 2560, 1, (256, 1), 8),
+    ("ISING1D", 3072, 1, (512, 1), 16),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1105_4673_gb300 import build
+    build.build()
+
+
+def _run(model, lx, ly, q, init, scheme, dt, T, seed, clock, engine, grouped, packed=False):
+    c = F.Context(lx, ly, model, RATES[model], q, bitpacked=packed)
+    try:
+        c.set_clock(clock)
+        c.set_engine(engine)
+        c.set_cell_grouping(grouped)
+        c.set_state(init)
+        c.run(scheme, dt, T, seed)
+        st = c.stats()
+        return c.get_state(), st, c.workload(), c.info()
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("model,lx,ly,q,lanes", GEOMS)
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_grouped_matches_oracle_fp64(model, lx, ly, q, lanes, engine):
+    seed = 0x6A0 + lx + ly
+    init = oracle.init_bernoulli(lx, ly, seed, 0.5)
+    dt, T = 0.1, 1.0
+    orc = oracle.FSRun(lx, ly, *q, model, RATES[model], init).run("LIE", dt, T, seed)
+    lat, st, wl, info = _run(model, lx, ly, q, init, "LIE", dt, T, seed, "FP64", engine, True)
+    assert info["lanes_per_cell"] == lanes
+    assert st["check_failures"] == 0 and st["timeouts"] == 0
+    assert st["events"] > 0
+    if orc.ambiguous == 0:
+        assert np.array_equal(lat, orc.lat)
+        assert st["events"] == orc.events
+        assert np.array_equal(wl, orc.workload)
+
+
+@pytest.mark.parametrize("model,lx,ly,q,lanes", GEOMS)
+@pytest.mark.parametrize("clock", ["FP64", "FP32"])
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_grouped_equals_one_cell_per_warp(model, lx, ly, q, lanes, clock, engine):
+    seed = 0x6A1 + lx
+    init = oracle.init_bernoulli(lx, ly, seed, 0.5)
+    a = _run(model, lx, ly, q, init, "RANDOM_ORDER", 0.2, 2.0, seed, clock, engine, True)
+    b = _run(model, lx, ly, q, init, "RANDOM_ORDER", 0.2, 2.0, seed, clock, engine, False)
+    assert a[3]["lanes_per_cell"] == lanes and b[3]["lanes_per_cell"] == 32
+    assert np.array_equal(a[0], b[0])
+    assert a[1]["events"] == b[1]["events"] and a[1]["events"] > 0
+    assert np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("clock", ["FP64", "FP32"])
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_grouped_packed_storage(clock, engine):
+    """Bit-packed lattice with 16-wide and 8-wide cells (two cells of a
+    warp, or a cell and its inactive neighbour, share a 32-bit word)."""
+    for lx, ly, q in ((256, 128, (16, 16)), (128, 64, (8, 8))):
+        seed = 0x6A2 + lx
+        init = oracle.init_bernoulli(lx, ly, seed, 0.5)
+        a = _run("ISING", lx, ly, q, init, "STRANG", 0.5, 3.0, seed, clock, engine, True, packed=True)
+        b = _run("ISING", lx, ly, q, init, "STRANG", 0.5, 3.0, seed, clock, engine, False, packed=False)
+        assert np.array_equal(a[0], b[0]) and a[1]["events"] == b[1]["events"]
+        if clock == "FP64":
+            orc = oracle.FSRun(lx, ly, *q, "ISING", RATES["ISING"], init).run("STRANG", 0.5, 3.0, seed)
+            if orc.ambiguous == 0:
+                assert np.array_equal(a[0], orc.lat) and a[1]["events"] == orc.events
+
+
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_grouped_uneven_cells_in_a_warp(engine):
+    """A Gaussian bump of occupied sites on an empty lattice: neighbouring
+    cells of one warp run very different numbers of events, so groups leave
+    the lockstep loop at very different iterations."""
+    lx, ly, q = 128, 128, (8, 8)
+    rates = dict(ka=0.05, kd=1.0, betaJ=3.0)
+    out = []
+    for grouped in (True, False):
+        with F.Context(lx, ly, "ADSDES", rates, q) as c:
+            c.set_engine(engine)
+            c.set_cell_grouping(grouped)
+            c.init_bump(5, 0.95, 12.0, 1)
+            init = c.get_state()
+            c.run("LIE", 0.5, 4.0, 17)
+            out.append((c.get_state(), c.stats()["events"], c.workload()))
+    wl = out[0][2]
+    assert wl.max() > 4 * max(1, np.median(wl))  # uneven indeed
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
+    orc = oracle.FSRun(lx, ly, *q, "ADSDES", rates, init).run("LIE", 0.5, 4.0, 17)
+    if orc.ambiguous == 0:
+        assert np.array_equal(out[0][0], orc.lat) and out[0][1] == orc.events
+
+
+@pytest.mark.parametrize("clock", ["FP64", "FP32"])
+def test_grouped_persistent_uneven_batch(clock):
+    """Replicas of different sizes and rates in one persistent launch: a
+    task's cells may straddle two replicas."""
+    reps = [dict(lx=32, ly=32, rates=dict(ka=0.5, kd=1.0, betaJ=0.3)),
+            dict(lx=64, ly=48, rates=dict(ka=2.0, kd=1.0, betaJ=0.8)),
+            dict(lx=48, ly=16, rates=dict(ka=1.0, kd=1.0, betaJ=0.0)),
+            dict(lx=16, ly=16, rates=dict(ka=0.1, kd=1.0, betaJ=0.5))]
+    seed = 77
+    res = []
+    for grouped in (True, False):
+        with F.Context(model="ADSDES", q=(8, 8), batch=reps) as b:
+            b.set_engine("PERSISTENT")
+            b.set_clock(clock)
+            b.set_cell_grouping(grouped)
+            b.init_random(seed, 0.5)
+            b.run("LIE", 0.1, 2.0, seed)
+            assert b.stats()["timeouts"] == 0
+            res.append(([b.get_state(r) for r in range(len(reps))], b.stats()["events"]))
+    for r in range(len(reps)):
+        assert np.array_equal(res[0][0][r], res[1][0][r]), f"replica {r}"
+    assert res[0][1] == res[1][1]
+
+
+def test_grouping_switch_rejects_bad_values():
+    with F.Context(64, 64, "ISING", RATES["ISING"], (8, 8)) as c:
+        with pytest.raises(F.FskmcError):
+            F._check(F.lib().fskmc_set_cell_grouping(c.h, 3), c.h)
+        assert c.info()["lanes_per_cell"] == 8  # auto: plain engine, binary64 clock
+        c.set_cell_grouping(False)
+        assert c.info()["lanes_per_cell"] == 32
+        c.set_cell_grouping(True)
+        c.set_engine("PERSISTENT")
+        assert c.info()["lanes_per_cell"] == 8
+        c.set_cell_grouping("AUTO")
+        assert c.info()["lanes_per_cell"] == 32  # 256 active cells: one wave
+    with F.Context(64, 64, "ZGB", dict(yA=0.5, kr=1.0, kd=0.0), (8, 8)) as c:
+        assert c.info()["lanes_per_cell"] == 32  # two-site models take a whole warp
