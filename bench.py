@@ -116,27 +116,34 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-# Roofline of the binary64 window kernel: it is bound by the FP64 pipe
-# (ncu: ~62% of its peak, the rest of the time the dependent chain).
-# Algorithmic binary64 operations per event of the contract, each a
-# warp-uniform instruction of the cell's warp: the ordered fused
-# multiply-add chain over the model's K classes, the divide, the threshold
-# multiply, the clock add and the logarithm.
+# Roofline of the window kernels. The per-event arithmetic of the clock
+# contract is K + 4 operations: the ordered fused multiply-add chain over
+# the model's K classes (binary64) or the exact fixed-point class sums
+# (binary32 clock), the threshold multiply, the clock add, the divide and
+# the logarithm. They are uniform within a cell, so one warp instruction
+# serves every cell that shares the warp: 1 in the one-cell kernels, 32 / W
+# in the grouped kernels (W lanes per cell). Algorithmic warp operations per
+# event = (K + 4) / cells per warp.
 NCLASSES = {"ADSDES": 10, "ISING": 10, "DIFFUSION": 15, "ZGB": 4, "ISING1D": 6}
-# Peak: the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp instructions,
-# 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
+# Peak (binary64): the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp
+# instructions, 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
 FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
-# The binary32 clock's per-event algorithmic work is the same contract with
-# integer class sums; its peak is the INT32/FP32 warp-instruction issue rate,
-# 152 SMs x 4 schedulers x 2.07 GHz.
+# Peak (binary32 clock): the warp-instruction issue rate, 152 SMs x 4
+# schedulers x 2.07 GHz.
 ISSUE_PEAK_G = 152 * 4 * 2.07
+# Measured dependent latency of one binary64 fused multiply-add on GB300
+# (cycles): the binary64 chain of K + 2 dependent operations per event is
+# the latency floor of the binary64 kernels.
+FP64_DEP_LATENCY_CYCLES = 64
 
-# DRAM traffic per launch of fs_window_kernel<ISING,double> (bit-packed
-# lattice) on this workload from one ncu capture
-# (profiles/fs_window_kernel_ising1024.md), valid only for the kernel source
-# it was taken on.
-PROFILED_TRAFFIC = {"src_sha256": "44964402c1044a6be28afbe38e47d517409eaaa898cf06d73d2d5a8349d8a5d5",
-                    "bytes_per_launch": 170240}
+# DRAM traffic per launch of the bench's kernel on the 1024^2 Ising workload
+# (bit-packed lattice) from one ncu capture (profiles/), valid only for the
+# kernel source it was taken on.
+PROFILED_TRAFFIC = {
+    "fs_group_kernel<ISING,double,packed,W=8>": {
+        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 176640,
+        "src_sha256": "733530ede0e6b4bf969689a75054aef25898b8684100231169494f02dd4938ad"},
+}
 
 
 def init_state(ctx, w, seed):
@@ -156,10 +163,24 @@ def stage_bytes_per_site(w):
     return ((1.0 + 2.0 / q) ** 2 + 1.0) / (8.0 if w.get("bitpacked") else 1.0)
 
 
-def window_src_sha():
+def src_sha(names):
+    """SHA-256 over the kernel's source files, in order."""
     import hashlib
-    path = os.path.join(ROOT, "paper_1105_4673_gb300", "csrc", "fskmc_window.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for name in names:
+        h.update(open(os.path.join(ROOT, "paper_1105_4673_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_name(engine, model, fp64, packed, lanes):
+    """The window kernel the bench's configuration launches."""
+    grouped = lanes < 32
+    base = {("plain", False): "fs_window_kernel", ("persistent", False): "fs_persistent_kernel",
+            ("plain", True): "fs_group_kernel", ("persistent", True): "fs_group_persistent_kernel"}
+    args = [model, "double" if fp64 else "float"] + (["packed"] if packed else [])
+    if grouped:
+        args.append(f"W={lanes}")
+    return f"{base[(engine, grouped)]}<{','.join(args)}>"
 
 
 def cpu_baseline(w, seconds):
@@ -322,16 +343,22 @@ def main():
     cs = clk.summary()
     k_events_per_launch = events / max(len(kernel_ms), 1)
     k_avg_s = float(np.mean(kernel_ms)) / 1000.0
+    lanes = ctx.info()["lanes_per_cell"]
+    cells_per_warp = 32 // lanes if lanes < 32 else 1
     ops_per_event = NCLASSES[w["model"]] + 4
-    achieved = k_events_per_launch * ops_per_event / k_avg_s / 1e9
+    warp_ops_per_event = ops_per_event / cells_per_warp
+    achieved = k_events_per_launch * warp_ops_per_event / k_avg_s / 1e9
     fp64 = args.clock == "fp64"
     peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
-    kname = ("fs_window_kernel" if args.engine == "plain" else "fs_persistent_kernel") + \
-        (f"<{w['model']},double>" if fp64 else f"<{w['model']},float>")
+    kname = kernel_name(args.engine, w["model"], fp64, bool(w.get("bitpacked")), lanes)
     traffic = None
-    if (args.engine == "plain" and fp64 and args.workload == "ising1024"
-            and PROFILED_TRAFFIC["src_sha256"] == window_src_sha()):
-        traffic = PROFILED_TRAFFIC["bytes_per_launch"]
+    prof = PROFILED_TRAFFIC.get(kname)
+    if prof and args.workload == "ising1024" and prof["src_sha256"] == src_sha(prof["src"]):
+        traffic = prof["bytes_per_launch"]
+    # the critical path: the slowest cell's events in the last window set the
+    # window's duration; cycles per event of that cell vs the binary64 floor
+    wl_max = int(ctx.workload(0).max()) if args.engine == "plain" else 0
+    sm_mhz = clk.summary().get("sm_mhz") or 2070.0
     cb = cpu_baseline(w, args.cpu_seconds)
     out = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
@@ -354,10 +381,17 @@ def main():
                      "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
                      "events_per_launch": k_events_per_launch,
                      "algorithmic_ops_per_event": ops_per_event,
+                     "cells_per_warp": cells_per_warp,
+                     "algorithmic_warp_ops_per_event": warp_ops_per_event,
                      "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
                                    if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz") +
                                   f"; HBM is not the bound ({stage_bytes_per_site(w):.2f} B per "
-                                  "active site per window)"},
+                                  "active site per window)",
+                     "critical_path": None if not wl_max else {
+                         "slowest_cell_events": wl_max,
+                         "cycles_per_event": k_avg_s * sm_mhz * 1e6 / wl_max,
+                         "binary64_floor_cycles_per_event":
+                             (NCLASSES[w["model"]] + 2) * FP64_DEP_LATENCY_CYCLES if fp64 else None}},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
                 "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
