@@ -162,13 +162,12 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
    32-site words rounded up to a power of two; at least 8 in 2D, 4 on a
    ring) and a warp runs 32/W cells of the same window in lockstep, so each
    instruction of the event loop (Eqs. totalrate and skeleton per cell)
-   serves 32/W cells. mode = 0: one
-   cell per warp. mode = 2 (default, auto): grouped when a window's active
-   cells are more than one wave of one-cell warps on the device, and in the
-   plain engine with the binary64 clock; otherwise one cell per warp. The
-   two-site models and larger cells always take a whole warp. Results
-   (lattices, event counts, workloads) do not depend on the mode. EINVAL:
-   mode outside 0..2. */
+   serves 32/W cells. mode = 0: one cell per warp. mode = 2 (default,
+   auto): grouped, except for the persistent engine with the binary64 clock
+   when all active cells fit in one wave of one-cell warps (there one cell
+   per warp is faster). The two-site models and larger cells always take a
+   whole warp. Results (lattices, event counts, workloads) do not depend on
+   the mode. EINVAL: mode outside 0..2. */
 fskmc_status fskmc_set_cell_grouping(fskmc_ctx *ctx, int32_t mode);
 
 /* Order in which the active cells of a window are issued (Section 6,

@@ -400,29 +400,22 @@ constexpr int ORDER_GROUP = 1024;
 // too short to pay for the ordering launch; the persistent engine's queue
 // overlaps windows.
 // Lanes per cell of the window kernels for this context and engine. AUTO
-// groups small cells when a window's active cells fill more than one wave of
-// one-cell warps (many warps then share each SM's issue slots and FP64 pipe,
-// and grouping divides that load), and in the plain engine with the binary64
-// clock (its FP64 pipe is busy even in one wave). A single wave in the
-// persistent engine keeps one cell per warp: there the cells of a warp would
-// wait for each other's neighbours, lengthening the chain of dependent
-// windows.
+// groups small cells, except in a single wave of the persistent engine with
+// the binary64 clock: there a warp's cells wait for each other's neighbours,
+// which lengthens the chain of dependent windows more than the grouping
+// saves (measured on the 1024^2 Ising workload: 8.0e8 events/s one cell per
+// warp vs 7.6e8 grouped; grouped wins in the plain engine and with the
+// binary32 clock, and whenever a window's cells exceed one wave).
 int lanes_per_cell(const fskmc_ctx *c, bool persistent)
 {
     const int W = fskmc::group_width(c->model, c->qx, c->qy);
     if (W >= 32 || c->grouping == 0) return 32;
     if (c->grouping == 1) return W;
     const int fp32 = c->clock == FSKMC_CLOCK_FP32;
-    if (!persistent && !fp32) return W;
-    int64_t active = 0;
-    if (persistent) {
-        active = c->total_cells / 2;
-    } else {
-        for (const Replica &R : c->reps) active = std::max<int64_t>(active, (int64_t)R.ncx * R.ncy / 2);
-    }
-    const int wpb = persistent ? std::min(c->wpb, 8) : c->wpb;
+    if (!persistent || fp32) return W;
+    const int wpb = std::min(c->wpb, 8);
     const int resident = fskmc::window_resident_warps(c->model, fp32, c->packed, c->qx, c->qy, wpb);
-    return active > resident ? W : 32;
+    return c->total_cells / 2 > resident ? W : 32;
 }
 
 bool use_order(const fskmc_ctx *c, int64_t active, bool persistent)

@@ -240,25 +240,33 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         }
         const int sl = (int)(e & (uint32_t)(W - 1));
         const uint32_t w3 = __shfl_sync(FULL, rw3, sl, W);
+        // The class, the member and the window-edge check of event e. In the
+        // plain engine the binary64 waiting time is divided by the
+        // branch-free Newton divide, which has no data dependence on the
+        // class choice and the rank search, so the three are written without
+        // branches and interleave (the plain engine's grouped windows are
+        // latency-bound). The persistent engine groups cells when a window
+        // has more cells than one wave, where the FP64 pipe's throughput
+        // counts, and divides on the integer pipes instead. The edge check is
+        // applied before anything is written.
         int k;
+        double lq = 0.0;  // binary64: -log(u_t) / lambda
+        bool slow = false;
+        double l = 0.0;
         if (F64) {
-            const double l = __shfl_sync(FULL, rl, sl, W);
+            l = __shfl_sync(FULL, rl, sl, W);
             const double uc = __shfl_sync(FULL, ruc, sl, W);
-            const double end = __dadd_rn(tau, div_rn(l, lamd));
-            const long long eb = dbits(end);
-            if (act && llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
-            if (eb >= hbits) act = false;
-            if (act) tau = end;
+            if (PERSIST) lq = div_rn(l, lamd);
+            else lq = div_newton(l, lamd, slow);
             const long long tb = dbits(__dmul_rn(uc, lamd));
-            k = K - 1;
+            k = 0;
 #pragma unroll
-            for (int kk = K - 2; kk >= 0; --kk)
-                if (tb < dbits(Pd[kk])) k = kk;
+            for (int kk = 0; kk < K - 1; ++kk) k += dbits(Pd[kk]) <= tb ? 1 : 0;  // P is non-decreasing
         } else {
-            const float l = __shfl_sync(FULL, rlf, sl, W);
+            const float lf = __shfl_sync(FULL, rlf, sl, W);
             const uint32_t w2 = __shfl_sync(FULL, rw2, sl, W);
             const float lamf = lami ? __fmul_rn(u64_to_float_rz(lami), qscale) : 0.0f;
-            const float end = __fadd_rn(tauf, __fdividef(l, lamf));
+            const float end = __fadd_rn(tauf, __fdividef(lf, lamf));
             if (end >= hf) act = false;
             if (act) tauf = end;
             const uint64_t t = (uint64_t)w2 * (lami >> 32) + (((uint64_t)w2 * (lami & 0xffffffffull)) >> 32);
@@ -274,26 +282,33 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         const int nk = cnt[k];
         const uint32_t j = (uint32_t)(((uint64_t)w3 * (uint64_t)(uint32_t)nk) >> 32);
 
-        // Rank search: the j-th member of class k in canonical order.
+        // Rank search: the j-th member of class k in canonical order (lanes
+        // past the cell's words hold zero words, so the full-width scan
+        // needs no branch).
         const uint32_t mw = gl < NL ? mask[k * W + gl] : 0u;
         const int c = __popc(mw);
         int incl = c;
 #pragma unroll
         for (int off = 1; off < W; off <<= 1) {
-            if (off < NL) {
-                const int v = __shfl_up_sync(FULL, incl, off, W);
-                if (gl >= off) incl += v;
-            }
+            const int v = __shfl_up_sync(FULL, incl, off, W);
+            incl += gl >= off ? v : 0;
         }
         const uint32_t hit = (__ballot_sync(FULL, (uint32_t)incl > j) >> gshift) & gbits;
+        const int owner = hit ? __ffs(hit) - 1 : 0;
+        const int pick = __shfl_sync(FULL, select_bit(mw, (int)j - (incl - c)), owner, W);
+
+        if (F64) {
+            if (act && slow) lq = __ddiv_rn(l, lamd);  // operands outside the normal range
+            const double end = __dadd_rn(tau, lq);
+            const long long eb = dbits(end);
+            if (act && llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+            if (eb >= hbits) act = false;
+            if (act) tau = end;
+        }
         if (act && hit == 0u) {  // counts and masks disagree: stop rather than write out of bounds
             bad = true;
             act = false;
         }
-        const int owner = hit ? __ffs(hit) - 1 : 0;
-        int pick = 0;
-        if (gl == owner) pick = select_bit(mw, (int)j - (incl - c));
-        pick = __shfl_sync(FULL, pick, owner, W);
 
         // Spin flip at the picked site: its class k = SK sigma + n becomes
         // k -+ SK, and each neighbour inside the cell changes n by +-1 (lanes

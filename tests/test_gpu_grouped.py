@@ -154,13 +154,15 @@ def test_grouping_switch_rejects_bad_values():
     with F.Context(64, 64, "ISING", RATES["ISING"], (8, 8)) as c:
         with pytest.raises(F.FskmcError):
             F._check(F.lib().fskmc_set_cell_grouping(c.h, 3), c.h)
-        assert c.info()["lanes_per_cell"] == 8  # auto: plain engine, binary64 clock
+        assert c.info()["lanes_per_cell"] == 8  # auto: plain engine
         c.set_cell_grouping(False)
         assert c.info()["lanes_per_cell"] == 32
         c.set_cell_grouping(True)
         c.set_engine("PERSISTENT")
         assert c.info()["lanes_per_cell"] == 8
         c.set_cell_grouping("AUTO")
-        assert c.info()["lanes_per_cell"] == 32  # 256 active cells: one wave
+        assert c.info()["lanes_per_cell"] == 32  # persistent, binary64, 256 active cells: one wave
+        c.set_clock("FP32")
+        assert c.info()["lanes_per_cell"] == 8
     with F.Context(64, 64, "ZGB", dict(yA=0.5, kr=1.0, kd=0.0), (8, 8)) as c:
         assert c.info()["lanes_per_cell"] == 32  # two-site models take a whole warp
