@@ -141,8 +141,8 @@ FP64_DEP_LATENCY_CYCLES = 64
 # kernel source it was taken on.
 PROFILED_TRAFFIC = {
     "fs_group_kernel<ISING,double,packed,W=8>": {
-        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 176640,
-        "src_sha256": "733530ede0e6b4bf969689a75054aef25898b8684100231169494f02dd4938ad"},
+        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 174848,
+        "src_sha256": "b69f58ee32c50f8173112cbf77e8fa284ddfcffe4666b05905b87edacb31bb54"},
 }
 
 

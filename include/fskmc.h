@@ -163,11 +163,10 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
    ring) and a warp runs 32/W cells of the same window in lockstep, so each
    instruction of the event loop (Eqs. totalrate and skeleton per cell)
    serves 32/W cells. mode = 0: one cell per warp. mode = 2 (default,
-   auto): grouped, except for the persistent engine with the binary64 clock
-   when all active cells fit in one wave of one-cell warps (there one cell
-   per warp is faster). The two-site models and larger cells always take a
-   whole warp. Results (lattices, event counts, workloads) do not depend on
-   the mode. EINVAL: mode outside 0..2. */
+   auto): the same as 1 (grouped cells were faster in every engine and clock
+   measured). The two-site models and larger cells always take a whole
+   warp. Results (lattices, event counts, workloads) do not depend on the
+   mode. EINVAL: mode outside 0..2. */
 fskmc_status fskmc_set_cell_grouping(fskmc_ctx *ctx, int32_t mode);
 
 /* Order in which the active cells of a window are issued (Section 6,
@@ -297,14 +296,15 @@ fskmc_status fskmc_sync(fskmc_ctx *ctx);
 /*
  * Self-test of the binary64 window clock's divides. The waiting time
  * -log(u_t)/lambda of the binary64 contract (Eqs. totalrate/skeleton) is
- * divided without the hardware divide: on the integer pipes (exact quotient
- * and remainder of the significands, rounded to nearest even; one-cell
- * kernels) or by a Newton-Raphson reciprocal with an exact integer
- * correction of the quotient (grouped kernels). This compares both with the
- * hardware correctly rounded divide on the n pairs (a[i] >= 0, b[i] > 0,
- * host arrays) and writes the number of disagreements (over both methods)
- * to *mismatches (must be 0). Runs on the current device. EINVAL: NULL
- * pointers, n < 0.
+ * divided without the hardware divide, on the integer pipes: a 64-bit
+ * reciprocal of the divisor's significand from a binary32 seed and two
+ * integer Newton-Raphson steps, the quotient by a multiply, then an exact
+ * remainder that corrects it and decides the rounding to nearest even. A
+ * binary64 Newton-Raphson variant is kept for comparison. This compares
+ * both (and the window kernels' wrapper with its hardware fallback) with
+ * the hardware correctly rounded divide on the n pairs (a[i] >= 0, b[i] > 0,
+ * host arrays) and writes the number of disagreements to *mismatches (must
+ * be 0). Runs on the current device. EINVAL: NULL pointers, n < 0.
  */
 fskmc_status fskmc_selftest_divide(const double *a, const double *b, int32_t n,
                                    uint32_t *mismatches);

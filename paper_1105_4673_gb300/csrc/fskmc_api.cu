@@ -399,23 +399,14 @@ constexpr int ORDER_GROUP = 1024;
 // order keeps neighbouring halos in cache; with few cells the windows are
 // too short to pay for the ordering launch; the persistent engine's queue
 // overlaps windows.
-// Lanes per cell of the window kernels for this context and engine. AUTO
-// groups small cells, except in a single wave of the persistent engine with
-// the binary64 clock: there a warp's cells wait for each other's neighbours,
-// which lengthens the chain of dependent windows more than the grouping
-// saves (measured on the 1024^2 Ising workload: 8.0e8 events/s one cell per
-// warp vs 7.6e8 grouped; grouped wins in the plain engine and with the
-// binary32 clock, and whenever a window's cells exceed one wave).
-int lanes_per_cell(const fskmc_ctx *c, bool persistent)
+// Lanes per cell of the window kernels for this context: grouped cells
+// wherever the model and cell size allow, unless grouping is switched off
+// (AUTO and ON agree: the grouped kernels were faster in every engine and
+// clock on the spin-flip workloads).
+int lanes_per_cell(const fskmc_ctx *c)
 {
     const int W = fskmc::group_width(c->model, c->qx, c->qy);
-    if (W >= 32 || c->grouping == 0) return 32;
-    if (c->grouping == 1) return W;
-    const int fp32 = c->clock == FSKMC_CLOCK_FP32;
-    if (!persistent || fp32) return W;
-    const int wpb = std::min(c->wpb, 8);
-    const int resident = fskmc::window_resident_warps(c->model, fp32, c->packed, c->qx, c->qy, wpb);
-    return c->total_cells / 2 > resident ? W : 32;
+    return (W >= 32 || c->grouping == 0) ? 32 : W;
 }
 
 bool use_order(const fskmc_ctx *c, int64_t active, bool persistent)
@@ -513,7 +504,7 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         pr.wpb = std::min(c->wpb, 8);  // the persistent kernel is built for <= 256 threads
         pr.spin_limit = c->spin_limit;
         pr.packed = c->packed;
-        pr.lanes_per_cell = lanes_per_cell(c, true);
+        pr.lanes_per_cell = lanes_per_cell(c);
         pr.order = nullptr;
         if (use_order(c, c->total_cells / 2, true)) {
             fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
@@ -538,7 +529,7 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
             fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
             if (st) return st;
         }
-        const int lanes = lanes_per_cell(c, false);
+        const int lanes = lanes_per_cell(c);
         for (size_t i = 0; i < nw; ++i) {
             fskmc_status st = plain_window(c, sched, i, c->w + i, seed, ordered, lanes);
             if (st) return st;
@@ -673,7 +664,7 @@ fskmc_status fskmc_info(const fskmc_ctx *c, int32_t out[6])
     out[2] = c->nrep;
     out[3] = c->total_cells;
     out[4] = c->wpb;
-    out[5] = lanes_per_cell(c, c->engine == FSKMC_ENGINE_PERSISTENT);
+    out[5] = lanes_per_cell(c);
     return FSKMC_OK;
 }
 

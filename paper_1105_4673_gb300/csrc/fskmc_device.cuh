@@ -164,41 +164,75 @@ __device__ __forceinline__ float u64_to_float_rz(uint64_t x)
     return __uint_as_float(((uint32_t)(190 - lz) << 23) | (m & 0x7FFFFFu));
 }
 
-// a / b rounded to nearest (ties to even) for a >= 0 and b > 0, computed on
-// the integer pipes: with 53-bit significands ma, mb the quotient
-// significand is Q = floor(ma 2^s / mb) in [2^52, 2^53) (s = 52 or 53) and
-// the exact remainder R = ma 2^s - Q mb decides the rounding (2R vs mb). On
-// GB300 the FP64 pipe is the window kernel's bottleneck; this keeps the
-// divide off it. Cases whose result would not be a normal number (or whose
-// divisor is subnormal) go to the hardware divide.
-__device__ double div_rn(double a, double b)
+// a / b rounded to nearest (ties to even) for a >= 0 and b > 0, on the
+// integer pipes and branch-free. With 53-bit significands ma, mb the quotient
+// significand is Q = floor(N / mb), N = ma 2^52 (ma >= mb) or ma 2^53, in
+// [2^52, 2^53). A 64-bit fixed-point reciprocal X ~ 2^116 / mb is seeded by
+// the binary32 reciprocal of mb's leading 24 bits (rcp.approx: relative error
+// about 2^-22) and refined by two Newton-Raphson steps
+// X <- X + X (2^116 - mb X) / 2^116 (each squares the relative error; the
+// residual is formed exactly from the 128-bit product mb X). The estimate
+// Q0 = (ma X) >> (116 - s) is then at most one below Q (checked on the CPU
+// in exact integer arithmetic for 2^-21 seed errors); the exact remainder
+// R = N - Q mb (its low 64 bits suffice, |R| < 2^63) corrects Q and decides
+// the rounding (2R against mb), as in long division. GB300's FP64 pipe is the
+// window kernels' scarcest unit; this keeps the divide off it. slow is set
+// for operands or quotients outside the normal range (zero, subnormal, huge),
+// where the caller uses the hardware divide.
+__device__ __forceinline__ double div_int(double a, double b, bool &slow)
 {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);
-    if (A == 0ull) return 0.0;
-    const long long ea = (long long)(A >> 52), eb = (long long)(B >> 52);
-    if (ea == 0 || eb == 0 || ea == 2047 || eb == 2047) return __ddiv_rn(a, b);
+    const int ea = (int)(A >> 52), eb = (int)(B >> 52);
     const unsigned long long FRAC = (1ull << 52) - 1ull;
     const unsigned long long ma = (A & FRAC) | (1ull << 52), mb = (B & FRAC) | (1ull << 52);
-    long long e = ea - eb + 1023;
-    unsigned __int128 N;
-    if (ma >= mb) {
-        N = (unsigned __int128)ma << 52;
-    } else {
-        N = (unsigned __int128)ma << 53;
-        e -= 1;
+    const float mf = __uint_as_float(0x3F800000u | (uint32_t)((B >> 29) & 0x7FFFFFu));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));
+    const uint32_t rb = __float_as_uint(rf);  // rf in (0.5, 1]: X0 = rf 2^64
+    unsigned long long X = (rb >> 23) >= 127u ? ~0ull
+                                               : (unsigned long long)((rb & 0x7FFFFFu) | 0x800000u) << 40;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const unsigned long long hi = __umul64hi(mb, X), lo = mb * X;
+        const unsigned long long T = (hi << 12) | (lo >> 52);  // (mb X) >> 52, mod 2^64
+        const long long E = (long long)(0ull - T);                // (2^116 - mb X) >> 52, signed
+        const unsigned long long corr = __umul64hi(X, E < 0 ? (unsigned long long)(-E) : (unsigned long long)E);
+        X = E < 0 ? X - corr - 1ull : X + corr;
     }
-    if (e < 1 || e > 2045) return __ddiv_rn(a, b);
-    unsigned long long Q = (unsigned long long)(N / mb);
-    const unsigned long long R = (unsigned long long)(N - (unsigned __int128)Q * mb);
-    if (2ull * R > mb || (2ull * R == mb && (Q & 1ull))) {
-        Q += 1ull;
-        if (Q == (1ull << 53)) {
-            Q >>= 1;
-            e += 1;
-        }
+    const bool ge = ma >= mb;
+    int e = ea - eb + (ge ? 1023 : 1022);
+    const unsigned long long qh = __umul64hi(ma, X), ql = ma * X;
+    unsigned long long Q = ge ? qh : ((qh << 1) | (ql >> 63));
+    long long R = (long long)((ma << (ge ? 52 : 53)) - Q * mb);
+    {
+        const bool neg = R < 0;
+        Q -= neg ? 1ull : 0ull;
+        R += neg ? (long long)mb : 0ll;
     }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool big = R >= (long long)mb;
+        Q += big ? 1ull : 0ull;
+        R -= big ? (long long)mb : 0ll;
+    }
+    const unsigned long long R2 = (unsigned long long)R << 1;
+    Q += (R2 > mb || (R2 == mb && (Q & 1ull))) ? 1ull : 0ull;
+    const bool carry = Q == (1ull << 53);
+    Q = carry ? (1ull << 52) : Q;
+    e += carry ? 1 : 0;
+    slow = ea == 0 || ea >= 2047 || eb == 0 || eb >= 2047 || e < 1 || e > 2046 || R < 0 ||
+           R >= (long long)mb;
     return __longlong_as_double((long long)(((unsigned long long)e << 52) | (Q & FRAC)));
+}
+
+// a / b rounded to nearest (ties to even) for a >= 0 and b > 0: div_int, with
+// the hardware divide for operands or quotients outside its range.
+__device__ __forceinline__ double div_rn(double a, double b)
+{
+    bool slow;
+    const double q = div_int(a, b, slow);
+    return slow ? __ddiv_rn(a, b) : q;
 }
 
 // a / b rounded to nearest (ties to even) for a >= 0 and b > 0 without a

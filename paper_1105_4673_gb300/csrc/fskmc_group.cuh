@@ -240,15 +240,11 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         }
         const int sl = (int)(e & (uint32_t)(W - 1));
         const uint32_t w3 = __shfl_sync(FULL, rw3, sl, W);
-        // The class, the member and the window-edge check of event e. In the
-        // plain engine the binary64 waiting time is divided by the
-        // branch-free Newton divide, which has no data dependence on the
-        // class choice and the rank search, so the three are written without
-        // branches and interleave (the plain engine's grouped windows are
-        // latency-bound). The persistent engine groups cells when a window
-        // has more cells than one wave, where the FP64 pipe's throughput
-        // counts, and divides on the integer pipes instead. The edge check is
-        // applied before anything is written.
+        // The class, the member and the window-edge check of event e. The
+        // binary64 waiting time is divided by the branch-free integer-pipe
+        // divide, which has no data dependence on the class choice and the
+        // rank search, so the three are written without branches and
+        // interleave; the edge check is applied before anything is written.
         int k;
         double lq = 0.0;  // binary64: -log(u_t) / lambda
         bool slow = false;
@@ -256,8 +252,7 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         if (F64) {
             l = __shfl_sync(FULL, rl, sl, W);
             const double uc = __shfl_sync(FULL, ruc, sl, W);
-            if (PERSIST) lq = div_rn(l, lamd);
-            else lq = div_newton(l, lamd, slow);
+            lq = div_int(l, lamd, slow);
             const long long tb = dbits(__dmul_rn(uc, lamd));
             k = 0;
 #pragma unroll

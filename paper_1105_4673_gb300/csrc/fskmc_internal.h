@@ -73,9 +73,6 @@ struct WindowArgs {
 
 // Shared-memory bytes one warp of the window kernel needs.
 size_t window_smem_per_warp(int model, int qx, int qy);
-// Warps of the one-cell window kernel that fit on the device at once with
-// wpb warps per block (0 if unknown).
-int window_resident_warps(int model, int fp32, bool packed, int qx, int qy, int wpb);
 
 // Lanes per cell of the grouped window kernels (several small cells per
 // warp, spin-flip models only): the lanes owning the cell's 32-site words,

@@ -870,17 +870,6 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
 }
 
 template <int MODEL>
-void *window_kernel_ptr(int fp32, bool packed)
-{
-    if constexpr (is_spin_flip<MODEL>()) {
-        if (packed)
-            return fp32 ? (void *)fs_window_kernel<MODEL, float, true>
-                        : (void *)fs_window_kernel<MODEL, double, true>;
-    }
-    return fp32 ? (void *)fs_window_kernel<MODEL, float, false> : (void *)fs_window_kernel<MODEL, double, false>;
-}
-
-template <int MODEL>
 void *persistent_kernel_ptr(int fp32, bool packed)
 {
     if constexpr (is_spin_flip<MODEL>()) {
@@ -905,29 +894,6 @@ void *persistent_kernel_for(int model, int fp32, bool packed)
 }
 
 }  // namespace
-
-int window_resident_warps(int model, int fp32, bool packed, int qx, int qy, int wpb)
-{
-    void *kern = nullptr;
-    switch (model) {
-    case ADSDES: kern = window_kernel_ptr<ADSDES>(fp32, packed); break;
-    case ISING: kern = window_kernel_ptr<ISING>(fp32, packed); break;
-    case DIFFUSION: kern = window_kernel_ptr<DIFFUSION>(fp32, false); break;
-    case ZGB: kern = window_kernel_ptr<ZGB>(fp32, false); break;
-    case ISING1D: kern = window_kernel_ptr<ISING1D>(fp32, packed); break;
-    }
-    const size_t smem = window_smem_per_warp(model, qx, qy) * (size_t)wpb;
-    int per_sm = 0, dev = 0, nsm = 0;
-    if (!kern || smem > 200 * 1024) return 0;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpb, smem) != cudaSuccess ||
-        cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    return per_sm * wpb * nsm;
-}
 
 size_t window_smem_per_warp(int model, int qx, int qy)
 {
@@ -1127,11 +1093,14 @@ __global__ void div_selftest_kernel(const double *a, const double *b, int n, uns
     if (i < n) {
         const double y = __ddiv_rn(a[i], b[i]);
         const double x = div_rn(a[i], b[i]);
-        bool slow;
+        bool slow, slow2;
         double z = div_newton(a[i], b[i], slow);
         if (slow) z = y;  // the caller's fallback
+        double u = div_int(a[i], b[i], slow2);
+        if (slow2) u = y;
         if (__double_as_longlong(x) != __double_as_longlong(y)) atomicAdd(bad, 1u);
         if (__double_as_longlong(z) != __double_as_longlong(y)) atomicAdd(bad, 1u);
+        if (__double_as_longlong(u) != __double_as_longlong(y)) atomicAdd(bad, 1u);
     }
 }
 

@@ -161,7 +161,7 @@ def test_grouping_switch_rejects_bad_values():
         c.set_engine("PERSISTENT")
         assert c.info()["lanes_per_cell"] == 8
         c.set_cell_grouping("AUTO")
-        assert c.info()["lanes_per_cell"] == 32  # persistent, binary64, 256 active cells: one wave
+        assert c.info()["lanes_per_cell"] == 8
         c.set_clock("FP32")
         assert c.info()["lanes_per_cell"] == 8
     with F.Context(64, 64, "ZGB", dict(yA=0.5, kr=1.0, kd=0.0), (8, 8)) as c:
