@@ -565,6 +565,82 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             }
             __syncwarp();
 
+            if (MODEL == ZGB) {
+                // ZGB: a site's class depends only on its own state and a
+                // slot's only on the states of its two ends, so only the
+                // changed sites' classes and the slots with an end at a changed
+                // site can change. Lanes 0-7 take the origin's four directions
+                // (the two directed slots between it and that neighbour), lanes
+                // 8-15 the target's (pair events; the bond between the two is
+                // left to the origin's lanes), lanes 16 and 17 the two sites'
+                // own classes.
+                const int grp = lane < 8 ? 0 : (lane < 16 ? 1 : 2);
+                const bool use_t = grp == 1 || lane == 17;
+                const int cxl = use_t ? tx : ox, cyl = use_t ? ty : oy;  // the changed site
+                const bool c_in = cxl >= 0 && cxl < qx && cyl >= 0 && cyl < qy;
+                const bool live = grp == 0 || lane == 16 || (slot && (grp == 1 || lane == 17));
+                if (grp == 2) {
+                    if (live && c_in) {
+                        const int i = cyl * qx + cxl;
+                        const int knew = site_class<MODEL>(box, BW, (cyl + HW) * BW + cxl + HW);
+                        const int kold = (int8_t)scls[i];
+                        if (knew != kold) {
+                            scls[i] = (uint8_t)knew;
+                            const uint32_t bit = 1u << (i & 31);
+                            if (kold >= 0) {
+                                atomicAnd(&sitemask[mask_of<MODEL>(kold) * 32 + (i >> 5)], ~bit);
+                                atomicSub(&cnt[kold], 1);
+                            }
+                            if (knew >= 0) {
+                                atomicOr(&sitemask[mask_of<MODEL>(knew) * 32 + (i >> 5)], bit);
+                                atomicAdd(&cnt[knew], 1);
+                            }
+                        }
+                    }
+                } else if (live) {
+                    const int dir = (lane & 7) >> 1, half = lane & 1;
+                    const int nx = cxl + dir_dx(dir), ny = cyl + dir_dy(dir);
+                    const bool n_in = nx >= 0 && nx < qx && ny >= 0 && ny < qy;
+                    const int opp = dir ^ 2;
+                    // the directed slot (member site s, slot d): outward s -> s+dir(d)
+                    // for d < 4, inward s+dir(d-4) -> s for d >= 4
+                    int sx_, sy_, d;
+                    bool any = true;
+                    if (grp == 1 && nx == ox && ny == oy) any = false;  // the pair's own bond
+                    if (c_in) {
+                        if (half == 0) { sx_ = cxl; sy_ = cyl; d = dir; }
+                        else if (n_in) { sx_ = nx; sy_ = ny; d = opp; }
+                        else { sx_ = cxl; sy_ = cyl; d = 4 + dir; }
+                    } else {
+                        any = any && n_in;
+                        sx_ = nx; sy_ = ny; d = half == 0 ? opp : 4 + opp;
+                    }
+                    if (any && slot_owned(sx_, sy_, d, qx, qy, colour)) {
+                        const int i = sy_ * qx + sx_;
+                        const int pu = (sy_ + HW) * BW + sx_ + HW;
+                        const int dd = d & 3;
+                        const int pn = pu + dir_dy(dd) * BW + dir_dx(dd);
+                        const int kn = d < 4 ? slot_class<MODEL>(box, BW, pu, pn) : slot_class<MODEL>(box, BW, pn, pu);
+                        const int bitpos = (i & 31) * 8 + d;
+                        const int wofs = (bitpos >> 5) * 32 + (i >> 5);
+                        const uint32_t bit = 1u << (bitpos & 31);
+                        int ko = -1;
+#pragma unroll
+                        for (int mbk = 0; mbk < TR::KB; ++mbk)
+                            if (slotmask[mbk * SW * 32 + wofs] & bit) ko = slot_class_of_mask<MODEL>(mbk);
+                        if (kn != ko) {
+                            if (ko >= 0) {
+                                atomicAnd(&slotmask[mask_of<MODEL>(ko) * SW * 32 + wofs], ~bit);
+                                atomicSub(&cnt[ko], 1);
+                            }
+                            if (kn >= 0) {
+                                atomicOr(&slotmask[mask_of<MODEL>(kn) * SW * 32 + wofs], bit);
+                                atomicAdd(&cnt[kn], 1);
+                            }
+                        }
+                    }
+                }
+            } else {
             // Refresh the classes of every own site within RR of the changed
             // sites, one site per lane (fixed region widths: 4 for RR = 1; 6 or
             // 5 for RR = 2 depending on the pair's orientation).
@@ -627,6 +703,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
                         }
                     }
                 }
+            }
             }
         }
         __syncwarp();
