@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--wpb", type=int, default=0, help="warps per CTA (0: the library default)")
     p.add_argument("--order", default="auto", choices=["auto", "natural", "workload"],
                    help="issue order of a window's active cells")
+    p.add_argument("--cell", type=int, default=0,
+                   help="ensemble512: square cell side (0: the library's autotuner picks cells and warps per CTA)")
     p.add_argument("--grouping", default="auto", choices=["auto", "on", "off"],
                    help="several small spin-flip cells per warp (on), one cell per warp (off), "
                         "or the library's choice (auto)")
@@ -204,8 +206,18 @@ def cpu_baseline(w, seconds):
                       f"of dt={w['dt']} ({run.events} events, {dt:.1f} s CPU, single thread)"}
 
 
+def ensemble_sample(w, reps, q):
+    """A single-lattice stand-in of the ensemble for the host-CPU oracle:
+    replica 0's rates, the ensemble's model, schedule and cells."""
+    return dict(model=w["model"], rates=reps[0]["rates"], q=tuple(q), scheme=w["scheme"], dt=w["dt"],
+                coverage=w["coverage"], seed=w["seed"])
+
+
 def run_reference(args, rank, world):
     w = WORKLOADS[args.workload]
+    if args.workload == "ensemble512":
+        from workloads import ensemble_replicas
+        w = ensemble_sample(w, ensemble_replicas(w["n"], w["seed"]), (16, 16))
     if rank != 0:
         return
     cb = None
@@ -238,11 +250,124 @@ def run_reference(args, rank, world):
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def run_ensemble(args, rank, world, local):
+    """The batched ensemble (512 replicas of uneven size and rates) advanced
+    in one persistent, graph-launched kernel per step; one step = 10 dt of
+    physical time for every replica. Cell size and warps per block come from
+    the library's autotuner."""
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    from workloads import ensemble_replicas
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS["ensemble512"]
+    seed = rank_seed(w["seed"], rank)
+    reps = ensemble_replicas(w["n"], w["seed"])
+    clock = args.clock.upper()
+    if args.cell:
+        q, wpb = (args.cell, args.cell), args.wpb or 2
+    else:
+        q, wpb, _ = F.autotune(reps, w["model"], w["scheme"], w["dt"], clock=clock, engine="PERSISTENT",
+                               coverage=w["coverage"], seed=w["seed"], stream=stream)
+    b = F.Context(model=w["model"], q=q, batch=reps, stream=stream)
+    b.set_engine("PERSISTENT")
+    b.set_warps_per_block(wpb)
+    b.set_clock(clock)
+    b.set_cell_grouping({"auto": "AUTO", "on": True, "off": False}[args.grouping])
+    b.init_random(seed, w["coverage"])
+    step_t = STEP_WINDOWS_DT * w["dt"]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        b.run(w["scheme"], w["dt"], step_t, seed)
+    torch.cuda.synchronize()
+    ev0 = b.stats()["events"]
+    barrier(world)
+    kev = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            b.run(w["scheme"], w["dt"], step_t, seed)
+            c.record(stream)
+            kev.append((a, c))
+        torch.cuda.synchronize()
+    barrier(world)
+    events = b.stats()["events"] - ev0
+    t_ms = max_over_ranks(sum(a.elapsed_time(c) for a, c in kev), world)
+    value = sum_over_ranks(events, world) / (t_ms / 1000.0)
+    # end to end: every replica's state in from pinned host memory, the step,
+    # every state out
+    hosts = [torch.empty(r["lx"] * r["ly"], dtype=torch.uint8, pin_memory=True) for r in reps]
+    for r, h in enumerate(hosts):
+        b.get_state(r, h.numpy())
+    torch.cuda.synchronize()
+    e_ev0 = b.stats()["events"]
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for r, h in enumerate(hosts):
+            b.set_state(h.numpy(), r)
+        b.run(w["scheme"], w["dt"], step_t, seed)
+        for r, h in enumerate(hosts):
+            b.get_state(r, h.numpy())
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_events = sum_over_ranks(b.stats()["events"] - e_ev0, world)
+    if rank != 0:
+        b.close()
+        return
+    fp64 = clock == "FP64"
+    lanes = b.info()["lanes_per_cell"]
+    cells_per_warp = 32 // lanes if lanes < 32 else 1
+    ops = NCLASSES[w["model"]] + 4
+    k_avg_s = t_ms / 1000.0 / args.steps
+    achieved = events / args.steps * ops / cells_per_warp / k_avg_s / 1e9
+    peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
+    nbytes = sum(r["lx"] * r["ly"] for r in reps)
+    cb = cpu_baseline(ensemble_sample(w, reps, q), args.cpu_seconds)
+    cb["sample"] = "replica 0's rates and the autotuned cells: " + cb["sample"]
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if fp64 else "f32+u64", "data": "synthetic",
+        "config": {"workload": f"ensemble512: {len(reps)} replicas, sides 64..512, {w['model']}, betaJ "
+                               f"U[0.2,0.8], ka/kd logU[0.1,10], {w['scheme']} dt={w['dt']}",
+                   "step": f"{step_t:g} time units for every replica, one persistent launch",
+                   "clock": args.clock, "engine": "persistent", "cell": f"{q[0]}x{q[1]}" + ("" if args.cell else " (autotuned)"),
+                   "warps_per_cta": wpb, "lanes_per_cell": lanes, "sites": nbytes,
+                   "cells": b.info()["cells"], "l2": "flushed between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "G fp64 warp-ops/s" if fp64 else "G warp-ops/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "kernel": kernel_name("persistent", w["model"], fp64, False, lanes),
+                     "kernel_ms_avg": k_avg_s * 1000, "launches": args.steps,
+                     "events_per_launch": events / args.steps, "algorithmic_ops_per_event": ops,
+                     "cells_per_warp": cells_per_warp,
+                     "algorithmic_warp_ops_per_event": ops / cells_per_warp,
+                     "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
+                                   if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz")},
+        "cpu_baseline": cb,
+        "e2e": {"value": e2e_events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }), flush=True)
+    b.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "ensemble512":
+        from paper_1105_4673_gb300 import build as B
+        B.build()
+        run_ensemble(args, rank, world, local)
         return
     import torch
 

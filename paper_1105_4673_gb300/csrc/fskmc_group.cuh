@@ -108,8 +108,10 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     // Stage the cell and its halo (periodic wrap) from the window-start
     // state; on the ring only the cell's own row.
     if (valid) {
+        // walk the box in row-major steps of W without dividing by its width
+        int by = ring ? HW : 0, bx = gl;
+        while (bx >= BW) { bx -= BW; ++by; }
         for (int i = gl; i < (ring ? BW : BW * BH); i += W) {
-            const int by = ring ? HW : i / BW, bx = ring ? i : i - by * BW;
             int gy = Y0 - HW + by, gx = X0 - HW + bx;
             gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
             gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
@@ -121,6 +123,8 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             } else {
                 box[bi] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
             }
+            bx += W;
+            while (bx >= BW) { bx -= BW; ++by; }
         }
     }
     for (int i = gl; i < MAX_CLASSES; i += W) cnt[i] = 0;  // a cell-less group keeps zero rates

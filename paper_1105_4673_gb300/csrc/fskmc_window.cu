@@ -117,18 +117,17 @@ __device__ void copy_unwritten(const uint8_t *src, uint8_t *dst, int lx, int ly,
                                int cx, int cy, int col, int lane)
 {
     const int X0 = cx * qx, Y0 = cy * qy;
-    if (col == 0) {
-        for (int i = lane; i < qy * (qx - 2); i += 32) {
-            int yy = Y0 + i / (qx - 2), xx = X0 + 1 + i % (qx - 2);
-            int64_t o = (int64_t)yy * lx + xx;
-            dst[o] = ld_site<PERSIST>(src + o);
-        }
-    } else {
-        for (int i = lane; i < qx * (qy - 2); i += 32) {
-            int yy = Y0 + 1 + i / qx, xx = X0 + i % qx;
-            int64_t o = (int64_t)yy * lx + xx;
-            dst[o] = ld_site<PERSIST>(src + o);
-        }
+    const int c0 = col == 0 ? 1 : 0, wdt = col == 0 ? qx - 2 : qx;  // columns c0 .. c0 + wdt - 1
+    const int r0 = col == 0 ? 0 : 1, nrow = col == 0 ? qy : qy - 2;  // rows r0 .. r0 + nrow - 1
+    if (wdt <= 0 || nrow <= 0) return;
+    // walk the region in row-major steps of 32 without dividing by its width
+    int r = r0, c = lane;
+    while (c >= wdt) { c -= wdt; ++r; }
+    for (int i = lane; i < wdt * nrow; i += 32) {
+        const int64_t o = (int64_t)(Y0 + r) * lx + X0 + c0 + c;
+        dst[o] = ld_site<PERSIST>(src + o);
+        c += 32;
+        while (c >= wdt) { c -= wdt; ++r; }
     }
 }
 
@@ -211,8 +210,10 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         // state; on the ring only the cell's own row (the rows above and
         // below are never read).
         constexpr bool ring = MODEL == ISING1D;
+        // walk the box in row-major steps of 32 without dividing by its width
+        int by = ring ? HW : 0, bx = lane;
+        while (bx >= BW) { bx -= BW; ++by; }
         for (int i = lane; i < (ring ? BW : BW * BH); i += 32) {
-            int by = ring ? HW : i / BW, bx = ring ? i : i - by * BW;
             int gy = Y0 - HW + by, gx = X0 - HW + bx;
             gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
             gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
@@ -224,6 +225,8 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             } else {
                 box[bi] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
             }
+            bx += 32;
+            while (bx >= BW) { bx -= BW; ++by; }
         }
     }
     for (int i = lane; i < Lo.sitemask_words + Lo.slotmask_words; i += 32) sitemask[i] = 0u;
