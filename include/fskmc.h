@@ -286,6 +286,17 @@ fskmc_status fskmc_observables(fskmc_ctx *ctx, int32_t replica, double *coverage
    library is broken). */
 fskmc_status fskmc_stats(fskmc_ctx *ctx, uint64_t out[5]);
 
+/* Window-edge decisions since creation that the binary64 clock took in
+   full (*out). The grouped spin-flip kernels take each decision (Eq.
+   skeleton: is tau + (-log u_t)/lambda past the window?) from a binary32
+   estimate of the waiting time on an exact integer clock with a running
+   error bound, and keep the binary64 clock tau a few events behind; an
+   event whose estimated end lies within that bound of the edge (about
+   2^-20 of the window length) is decided from tau in binary64 on the spot.
+   Results are the same either way; this counts those events. The other
+   kernels and the binary32 clock always decide in their own clock. */
+fskmc_status fskmc_exact_edge_checks(fskmc_ctx *ctx, uint64_t *out);
+
 /* Workload W(m) of Eq. wload: events each cell of a replica executed in its
    most recent window, out[ncx*ncy], cell id m = cy*ncx + cx. */
 fskmc_status fskmc_workload(fskmc_ctx *ctx, int32_t replica, int32_t *out);

@@ -35,7 +35,7 @@ EXPORTS = [
     "fskmc_set_replica_id", "fskmc_set_clock", "fskmc_set_engine", "fskmc_set_warps_per_block",
     "fskmc_set_cell_grouping", "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
-    "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_workload", "fskmc_sync",
+    "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_exact_edge_checks", "fskmc_workload", "fskmc_sync",
     "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_selftest_log",
     "fskmc_schedule",
 ]
@@ -100,6 +100,7 @@ def lib():
             "fskmc_observables": ([vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.c_int32], C.c_int),
             "fskmc_stats": ([vp, C.POINTER(C.c_uint64)], C.c_int),
+            "fskmc_exact_edge_checks": ([vp, C.POINTER(C.c_uint64)], C.c_int),
             "fskmc_workload": ([vp, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_sync": ([vp], C.c_int),
             "fskmc_selftest_divide": ([vp, vp, C.c_int32, C.POINTER(C.c_uint32)], C.c_int),
@@ -276,8 +277,10 @@ class Context:
     def stats(self) -> dict:
         out = (C.c_uint64 * 5)()
         _check(lib().fskmc_stats(self.h, out), self.h)
+        rr = C.c_uint64()
+        _check(lib().fskmc_exact_edge_checks(self.h, C.byref(rr)), self.h)
         return dict(events=out[0], windows=out[1], ambiguous=out[2], timeouts=out[3],
-                    check_failures=out[4])
+                    check_failures=out[4], exact_edge_checks=rr.value)
 
     def workload(self, replica: int = 0) -> np.ndarray:
         info = self.info()

@@ -32,7 +32,7 @@ struct fskmc_ctx {
     int64_t total_sites = 0;
     int32_t total_cells = 0;
     int32_t *d_workload = nullptr;
-    unsigned long long *d_counters = nullptr;  // events, ambiguous, timeouts, spare
+    unsigned long long *d_counters = nullptr;  // events, ambiguous, timeouts, check failures, binary64 edge checks
     unsigned int *d_scratch_u32 = nullptr;
     unsigned long long *d_obs = nullptr;
     int obs_cap = 0;
@@ -355,7 +355,7 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
     if (e == cudaSuccess && (int)model == fskmc::DIFFUSION) e = cudaMalloc(&c->d_lat[1], (size_t)off);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_reps, sizeof(Replica) * n);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_workload, sizeof(int32_t) * (size_t)coff);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * 5);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch_u32, sizeof(unsigned int) * 4);
     if (e == cudaSuccess && c->packed) e = cudaMalloc(&c->d_stage, (size_t)max_sites);
     if (e != cudaSuccess) {
@@ -366,7 +366,7 @@ fskmc_status make_ctx(int n, const fskmc_lattice *lats, fskmc_model model,
     e = cudaMemsetAsync(c->d_lat[0], 0, (size_t)off, c->stream);
     if (e == cudaSuccess && c->d_lat[1]) e = cudaMemsetAsync(c->d_lat[1], 0, (size_t)off, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_workload, 0, sizeof(int32_t) * (size_t)coff, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * 5, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_reps, c->reps.data(), sizeof(Replica) * n, cudaMemcpyHostToDevice,
                             c->stream);
@@ -842,6 +842,16 @@ fskmc_status fskmc_stats(fskmc_ctx *c, uint64_t out[5])
     out[2] = h[1];
     out[3] = h[2];
     out[4] = h[3];
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_exact_edge_checks(fskmc_ctx *c, uint64_t *out)
+{
+    if (!c || !out) return FSKMC_EINVAL;
+    unsigned long long h;
+    CK(c, cudaMemcpyAsync(&h, c->d_counters + 4, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *out = h;
     return FSKMC_OK;
 }
 

@@ -70,7 +70,9 @@ __host__ __device__ inline GLayout make_glayout(int qx, int qy, int W)
 
 // One group's fractional window (W lanes; every lane of the warp calls this
 // together). valid = the group has a cell. Outputs (group-uniform): events,
-// whether an edge decision was ambiguous, whether a consistency check failed.
+// whether an edge decision was ambiguous, whether a consistency check failed,
+// how many edge decisions the screened binary64 check left to the binary64
+// clock.
 // The class data are lane-parallel: lane l holds classes l, l + W, ... for
 // the fixed-point prefix sums (width-W shuffle scans), converts their counts
 // to binary64 for the ordered fused multiply-add chain (which every lane then
@@ -79,7 +81,7 @@ template <int MODEL, typename CLK, bool PERSIST, bool PACKED, int W>
 __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, const CellGeom &G,
                              bool valid, int cx, int cy, uint32_t w, double hwin, uint64_t seed,
                              const uint8_t *src, uint8_t *dst, int lane, uint32_t *ev_out,
-                             bool *amb_out, bool *bad_out)
+                             bool *amb_out, bool *bad_out, uint32_t *nexact_out)
 {
     using TR = Traits<MODEL>;
     static_assert(is_spin_flip<MODEL>(), "grouped cells are built for the spin-flip models");
@@ -183,6 +185,34 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     float rlf = 0.0f;
     const uint32_t ctr3 = R.rep | (TAG_EVENT << 24);
 
+    // Binary64 clock, screened edge check. Each event's window-edge
+    // decision (end = tau + (-log u_t) / lambda against h) is taken from a
+    // bounded estimate that needs no binary64 divide: the waiting time in
+    // binary32 (l rounded toward zero over lambda truncated to binary32, a
+    // reciprocal within one unit in the last place, three rounded products:
+    // at most 4.5 2^-23 relative error) on an exact 64-bit integer clock in
+    // units of h 2^-62, with a running bound E on its distance from the
+    // binary64 clock (2^-20 of each estimate, plus 2^11 units per event for
+    // the integer truncation and the binary64 roundings). An event is taken
+    // if clock + estimate + E < 2^62 and refused if clock + estimate >=
+    // 2^62 + E: the binary64 decision in both cases. The binary64 clock tau
+    // itself runs W events behind, off the critical path: at the start of
+    // each batch of W events, lane i divides event i's l by its lambda for
+    // the batch just ended, and iteration i of the next batch adds that
+    // waiting time to tau, in event order. An event the estimate cannot
+    // decide (an end within about 2^-20 h of the edge, or lambda outside
+    // the binary32 range; about one per thousand cell-windows) catches up a
+    // copy of tau and decides in binary64 on the spot; once such an event is
+    // taken, so are the group's remaining decisions of the window (the
+    // integer clock may then stand past 2^62).
+    const bool screen_ok = hwin > 1e-15 && hwin < 1e15;
+    const float sf = screen_ok ? (float)(0x1p62 / hwin) : 0.0f;
+    uint64_t clk = 0, err = 0;
+    double lam_mine = 1.0, lq_prev = 0.0;  // lane i: event i of the batch
+    int ntaken_cur = 0, ntaken_prev = 0;   // events taken in this batch, in the previous one
+    uint32_t nexact = 0;
+    bool near_edge = false;
+
     // Every running group executes event e in iteration e, so e is the same
     // for all of them and the draw batches stay aligned.
     for (uint32_t e = 0;; ++e) {
@@ -229,34 +259,58 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             bad = bad || act;
             act = false;
         }
-        if ((e & (uint32_t)(W - 1)) == 0u) {
+        const int sl = (int)(e & (uint32_t)(W - 1));
+        if (sl == 0) {
+            if (F64) {
+                // binary64 waiting times of the batch just ended, one event per lane
+                const bool mine = gl < ntaken_cur;
+                lq_prev = div_rn(mine ? rl : 1.0, mine ? lam_mine : 1.0);
+                ntaken_prev = ntaken_cur;
+                ntaken_cur = 0;
+            }
             // W events' draws at once, one Philox block per lane
             const u32x4 o = draw(seed, e + (uint32_t)gl, w, (uint32_t)m, ctr3);
             if (F64) {
                 const uint64_t b = ((uint64_t)o.x << 21) | (uint64_t)(o.y >> 11);
                 rl = neg_log_u53(b + 1ull);
                 ruc = u53_scaled(2ull * o.z + 1ull, 33);  // (o.z + 1/2) 2^-32
+                rlf = __double2float_rz(rl);
             } else {
                 rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
             }
             rw2 = o.z;
             rw3 = o.w;
         }
-        const int sl = (int)(e & (uint32_t)(W - 1));
         const uint32_t w3 = __shfl_sync(FULL, rw3, sl, W);
-        // The class, the member and the window-edge check of event e. The
-        // binary64 waiting time is divided by the branch-free integer-pipe
-        // divide, which has no data dependence on the class choice and the
-        // rank search, so the three are written without branches and
-        // interleave; the edge check is applied before anything is written.
+        // The class, the member and the window-edge check of event e: the
+        // edge estimate has no data dependence on the class choice and the
+        // rank search, so the three interleave; the edge check is applied
+        // before anything is written.
         int k;
-        double lq = 0.0;  // binary64: -log(u_t) / lambda
-        bool slow = false;
-        double l = 0.0;
+        uint64_t Qs = 0, Es = 0;
+        bool take = false, unsure = false;
         if (F64) {
-            l = __shfl_sync(FULL, rl, sl, W);
+            {  // the binary64 clock, W events behind
+                const double v = __shfl_sync(FULL, lq_prev, sl, W);
+                if (sl < ntaken_prev) tau = __dadd_rn(tau, v);
+            }
+            if (gl == sl) lam_mine = lamd;
             const double uc = __shfl_sync(FULL, ruc, sl, W);
-            lq = div_int(l, lamd, slow);
+            const float lf = __shfl_sync(FULL, rlf, sl, W);
+            const uint64_t lb = (uint64_t)dbits(lamd);
+            const int fe = (int)(lb >> 52) - 896;  // binary32 exponent field of lambda
+            const bool inrange = screen_ok && fe >= 1 && fe <= 250;
+            const float lamf = __uint_as_float(((uint32_t)fe << 23) | (uint32_t)((lb >> 29) & 0x7FFFFFu));
+            float rr;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(lamf));
+            const uint32_t qb = __float_as_uint(__fmul_rn(__fmul_rn(lf, rr), sf));
+            const int qe = (int)(qb >> 23) - 150;  // estimate = (24-bit significand) 2^qe
+            const uint64_t qm = (uint64_t)((qb & 0x7FFFFFu) | 0x800000u);
+            Qs = qe >= 40 ? (1ull << 63) : (qe >= 0 ? qm << qe : (qe > -24 ? qm >> -qe : 0ull));
+            Es = err + (Qs >> 20) + 2048ull;
+            const uint64_t rem = (1ull << 62) - clk;
+            take = inrange && Qs + Es < rem;
+            unsure = near_edge || !inrange || (!take && Qs < rem + Es);
             const long long tb = dbits(__dmul_rn(uc, lamd));
             k = 0;
 #pragma unroll
@@ -297,12 +351,36 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         const int pick = __shfl_sync(FULL, select_bit(mw, (int)j - (incl - c)), owner, W);
 
         if (F64) {
-            if (act && slow) lq = __ddiv_rn(l, lamd);  // operands outside the normal range
-            const double end = __dadd_rn(tau, lq);
-            const long long eb = dbits(end);
-            if (act && llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
-            if (eb >= hbits) act = false;
-            if (act) tau = end;
+            if (__any_sync(FULL, act && unsure)) {
+                // binary64 decision: tau up to event e - 1 (the rest of the
+                // previous batch, then this batch's events before e, all
+                // taken), plus event e's waiting time
+                double t = tau;
+                for (int i = 1; i < W; ++i) {
+                    const double v = __shfl_sync(FULL, lq_prev, i, W);
+                    if (i > sl && i < ntaken_prev) t = __dadd_rn(t, v);
+                }
+                const bool mine = gl <= sl;
+                const double lqc = div_rn(mine ? rl : 1.0, mine ? lam_mine : 1.0);
+                for (int i = 0; i < W - 1; ++i) {
+                    const double v = __shfl_sync(FULL, lqc, i, W);
+                    if (i < sl) t = __dadd_rn(t, v);
+                }
+                const double end = __dadd_rn(t, __shfl_sync(FULL, lqc, sl, W));
+                const long long eb = dbits(end);
+                if (act && unsure) {
+                    if (llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+                    take = eb < hbits;
+                    near_edge = true;
+                    ++nexact;
+                }
+            }
+            if (!take) act = false;
+            if (act) {
+                clk += Qs;
+                err = Es;
+                ++ntaken_cur;
+            }
         }
         if (act && hit == 0u) {  // counts and masks disagree: stop rather than write out of bounds
             bad = true;
@@ -374,22 +452,25 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     *ev_out = ev;
     *amb_out = amb;
     *bad_out = bad;
+    *nexact_out = nexact;
 }
 
-// Totals of a warp's groups: events, ambiguous and failed cell-windows (one
-// atomic each per warp).
+// Totals of a warp's groups: events, ambiguous and failed cell-windows,
+// edge decisions taken in binary64 (one atomic each per warp).
 template <int W>
 __device__ __forceinline__ void add_counters(unsigned long long *counters, int lane, bool valid,
-                                             uint32_t ev, bool amb, bool bad)
+                                             uint32_t ev, bool amb, bool bad, uint32_t nexact)
 {
     const bool lead = valid && (lane & (W - 1)) == 0;
     const uint32_t tot = __reduce_add_sync(FULL, lead ? ev : 0u);
     const int na = __popc(__ballot_sync(FULL, lead && amb));
     const int nb = __popc(__ballot_sync(FULL, lead && bad));
+    const uint32_t nr = __reduce_add_sync(FULL, lead ? nexact : 0u);
     if (lane == 0) {
         atomicAdd(&counters[0], (unsigned long long)tot);
         if (na) atomicAdd(&counters[1], (unsigned long long)na);
         if (nb) atomicAdd(&counters[3], (unsigned long long)nb);
+        if (nr) atomicAdd(&counters[4], (unsigned long long)nr);
     }
 }
 
@@ -422,12 +503,13 @@ __global__ void __launch_bounds__(256) fs_group_kernel(WindowArgs a, int nactive
     const GLayout Lo = make_glayout<MODEL>(a.geom.qx, a.geom.qy, W);
     uint8_t *csm = smem + (size_t)(wib * GC + lane / W) * stride;
     uint32_t ev;
+    uint32_t nexact;
     bool amb, bad;
     group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cx, cy, a.w, a.h, a.seed,
                                                 a.src + R.lat_off, a.dst + R.lat_off, lane, &ev,
-                                                &amb, &bad);
+                                                &amb, &bad, &nexact);
     if (valid && (lane & (W - 1)) == 0) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)ev;
-    add_counters<W>(a.counters, lane, valid, ev, amb, bad);
+    add_counters<W>(a.counters, lane, valid, ev, amb, bad, nexact);
 }
 
 // Persistent engine (in-place spin-flip models): a task is a chunk of GC
@@ -508,11 +590,13 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
         if (!ok) break;
 
         uint32_t ev;
+        uint32_t nexact;
         bool amb, bad;
         group_window<MODEL, CLK, true, PACKED, W>(csm, Lo, R, P.geom, valid, cx, cy, P.w0 + (uint32_t)i,
-                                                   P.h[i], P.seed, cur, cur, lane, &ev, &amb, &bad);
+                                                   P.h[i], P.seed, cur, cur, lane, &ev, &amb, &bad,
+                                                   &nexact);
         if (valid && gl == 0) P.workload[R.cell_off + m] = (int32_t)ev;
-        add_counters<W>(P.counters, lane, valid, ev, amb, bad);
+        add_counters<W>(P.counters, lane, valid, ev, amb, bad, nexact);
         __syncwarp();
         if (valid && gl == 0) {
             __threadfence();

@@ -72,6 +72,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.fskmc_run(None, 0, 0.1, 1.0, 1) == F.EINVAL
     assert lib.fskmc_sync(None) == F.EINVAL
     assert lib.fskmc_stats(None, None) == F.EINVAL
+    assert lib.fskmc_exact_edge_checks(None, None) == F.EINVAL
     lib.fskmc_destroy(None)
 
 
