@@ -214,24 +214,44 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     bool near_edge = false;
 
     // Every running group executes event e in iteration e, so e is the same
-    // for all of them and the draw batches stay aligned.
+    // for all of them and the draw batches stay aligned. The persistent
+    // kernel, which keeps many warps per SM busy and is bound by issue, asks
+    // whether any group is still running once per iteration, after the
+    // window-edge checks, so that the last iteration of a window stops
+    // before its class choice and rank search; the plain kernel, bound by
+    // the latency of one warp's chain, asks at the top.
     for (uint32_t e = 0;; ++e) {
-        if (!__any_sync(FULL, act)) break;
+        if (!PERSIST && !__any_sync(FULL, act)) break;
         double Pd[K];
         double lamd = 0.0;
         uint64_t P[CPL];
         uint64_t lami = 0;
         if (F64) {
+            if (PERSIST) {
 #pragma unroll
-            for (int s = 0; s < CPL; ++s) {
-                const int k = gl + W * s;
-                if (k < K) dcnt[k] = small_to_double(cnt[k]);  // one conversion per class, lane-parallel
-            }
-            __syncwarp();
+                for (int s = 0; s < CPL; ++s) {
+                    const int k = gl + W * s;
+                    if (k < K) dcnt[k] = small_to_double(cnt[k]);  // one conversion per class, lane-parallel
+                }
+                __syncwarp();
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                lamd = __fma_rn(dcnt[k], rk[k], lamd);  // fma(0, r, x) == x
-                Pd[k] = lamd;
+                for (int k = 0; k < K; ++k) {
+                    lamd = __fma_rn(dcnt[k], rk[k], lamd);  // fma(0, r, x) == x
+                    Pd[k] = lamd;
+                }
+            } else {
+                // every lane converts all counts itself: fewer steps before the chain
+                int cc[MAX_CLASSES];
+#pragma unroll
+                for (int q4 = 0; q4 < MAX_CLASSES; q4 += 4) {
+                    const int4 v = *reinterpret_cast<const int4 *>(cnt + q4);
+                    cc[q4] = v.x; cc[q4 + 1] = v.y; cc[q4 + 2] = v.z; cc[q4 + 3] = v.w;
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    lamd = __fma_rn(small_to_double(cc[k]), rk[k], lamd);
+                    Pd[k] = lamd;
+                }
             }
             if (dbits(lamd) == 0) act = false;
         } else {
@@ -311,6 +331,10 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             const uint64_t rem = (1ull << 62) - clk;
             take = inrange && Qs + Es < rem;
             unsure = near_edge || !inrange || (!take && Qs < rem + Es);
+            if (PERSIST) {
+                if (!take && !unsure) act = false;  // the event lies past the edge
+                if (!__any_sync(FULL, act)) break;
+            }
             const long long tb = dbits(__dmul_rn(uc, lamd));
             k = 0;
 #pragma unroll
@@ -322,6 +346,7 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             const float end = __fadd_rn(tauf, __fdividef(lf, lamf));
             if (end >= hf) act = false;
             if (act) tauf = end;
+            if (PERSIST && !__any_sync(FULL, act)) break;
             const uint64_t t = (uint64_t)w2 * (lami >> 32) + (((uint64_t)w2 * (lami & 0xffffffffull)) >> 32);
             k = -1;
 #pragma unroll

@@ -208,3 +208,32 @@ def test_screened_edge_check_matches_binary64(model, lx, ly, q, rates, dt, engin
     assert sa["events"] == sb["events"] and sa["ambiguous"] == sb["ambiguous"]
     assert np.array_equal(la, lb)
     assert np.array_equal(wa, wb)
+
+
+@pytest.mark.parametrize("model,rates", [
+    ("ADSDES", dict(ka=0.75, kd=0.5, betaJ=0.0)),      # every class rate dyadic
+    ("ADSDES", dict(ka=0.0, kd=3.0, betaJ=0.25)),      # a zero rate, then one dyadic class
+    ("ISING", dict(ka=1.0, kd=1.0, betaJ=0.4407)),     # five unit rates, then binary64
+    ("ISING", dict(ka=1.5, kd=2.0 ** -30, betaJ=0.0)),  # dyadic rates far apart
+])
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_dyadic_and_zero_rates_match_oracle(model, rates, engine):
+    """Dyadic rates (every fused multiply-add of the class sums exact, or
+    only the leading ones), a zero rate and rates far apart: the grouped
+    binary64 kernels give the same lattices and events as the oracle and
+    the one-cell kernels."""
+    lx, ly, q = 96, 64, (16, 16)
+    seed = 0x7E5
+    init = oracle.init_bernoulli(lx, ly, seed, 0.5)
+    res = []
+    for grouped in (True, False):
+        with F.Context(lx, ly, model, rates, q) as c:
+            c.set_engine(engine)
+            c.set_cell_grouping(grouped)
+            c.set_state(init)
+            c.run("STRANG", 0.5, 3.0, seed)
+            res.append((c.get_state(), c.stats()["events"]))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] > 0
+    orc = oracle.FSRun(lx, ly, *q, model, rates, init).run("STRANG", 0.5, 3.0, seed)
+    if orc.ambiguous == 0:
+        assert np.array_equal(res[0][0], orc.lat) and res[0][1] == orc.events
