@@ -143,8 +143,8 @@ FP64_DEP_LATENCY_CYCLES = 64
 # kernel source it was taken on.
 PROFILED_TRAFFIC = {
     "fs_group_kernel<ISING,double,packed,W=8>": {
-        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 174848,
-        "src_sha256": "b69f58ee32c50f8173112cbf77e8fa284ddfcffe4666b05905b87edacb31bb54"},
+        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 181760,
+        "src_sha256": "2b4cd5c821ca1f39291359b7db7f466ef6abd502734be9783ac4d8a96c0e153b"},
 }
 
 
