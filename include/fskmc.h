@@ -169,6 +169,18 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
    mode. EINVAL: mode outside 0..2. */
 fskmc_status fskmc_set_cell_grouping(fskmc_ctx *ctx, int32_t mode);
 
+/* Binary64 clock: how the window-edge decision of each event (Eq. skeleton:
+   is tau + (-log u_t)/lambda past the window?) is taken. 1 (default): from a
+   binary32 estimate of the waiting time on an exact integer clock with a
+   running error bound, the binary64 clock kept a few events behind and used
+   only for the events the estimate cannot decide (fskmc_exact_edge_checks
+   counts them); 0: every decision from the binary64 clock, caught up for
+   each event (a slow checking mode). Results (lattices, event counts,
+   workloads, ambiguity counts) do not depend on it. No effect with the
+   binary32 clock or in the persistent one-cell kernels (two-site models,
+   grouping off), which always divide in binary64. EINVAL: on not 0 or 1. */
+fskmc_status fskmc_set_edge_screen(fskmc_ctx *ctx, int32_t on);
+
 /* Order in which the active cells of a window are issued (Section 6,
    Eq. wload). The paper rebalances by reshaping the cells so that each
    processor receives equal work; here the cells keep their shape and the
@@ -287,14 +299,17 @@ fskmc_status fskmc_observables(fskmc_ctx *ctx, int32_t replica, double *coverage
 fskmc_status fskmc_stats(fskmc_ctx *ctx, uint64_t out[5]);
 
 /* Window-edge decisions since creation that the binary64 clock took in
-   full (*out). The grouped spin-flip kernels take each decision (Eq.
-   skeleton: is tau + (-log u_t)/lambda past the window?) from a binary32
-   estimate of the waiting time on an exact integer clock with a running
-   error bound, and keep the binary64 clock tau a few events behind; an
-   event whose estimated end lies within that bound of the edge (about
-   2^-20 of the window length) is decided from tau in binary64 on the spot.
-   Results are the same either way; this counts those events. The other
-   kernels and the binary32 clock always decide in their own clock. */
+   full (*out). The binary64-clock window kernels of the plain engine and
+   the grouped persistent kernels take each decision (Eq. skeleton: is
+   tau + (-log u_t)/lambda past the window?) from a binary32 estimate of the
+   waiting time on an exact integer clock with a running error bound, and
+   keep the binary64 clock tau a few events behind; an event whose estimated
+   end lies within that bound of the edge (about 2^-20 of the window length)
+   is decided from tau in binary64 on the spot. Results are the same either
+   way; this counts those decisions, and every decision of the persistent
+   one-cell kernels (which divide in binary64 for each event) and of windows
+   run with the screen off (fskmc_set_edge_screen). The binary32 clock
+   counts none. */
 fskmc_status fskmc_exact_edge_checks(fskmc_ctx *ctx, uint64_t *out);
 
 /* Workload W(m) of Eq. wload: events each cell of a replica executed in its

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5:
 EXPORTS = [
     "fskmc_create", "fskmc_batch_create", "fskmc_destroy", "fskmc_last_error",
     "fskmc_set_replica_id", "fskmc_set_clock", "fskmc_set_engine", "fskmc_set_warps_per_block",
-    "fskmc_set_cell_grouping", "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
+    "fskmc_set_cell_grouping", "fskmc_set_edge_screen", "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_exact_edge_checks", "fskmc_workload", "fskmc_sync",
     "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_selftest_log",
@@ -86,6 +86,7 @@ def lib():
             "fskmc_set_engine": ([vp, C.c_int], C.c_int),
             "fskmc_set_warps_per_block": ([vp, C.c_int32], C.c_int),
             "fskmc_set_cell_grouping": ([vp, C.c_int32], C.c_int),
+            "fskmc_set_edge_screen": ([vp, C.c_int32], C.c_int),
             "fskmc_set_spin_limit": ([vp, C.c_uint32], C.c_int),
             "fskmc_set_task_order": ([vp, C.c_int], C.c_int),
             "fskmc_info": ([vp, C.POINTER(C.c_int32)], C.c_int),
@@ -214,6 +215,11 @@ class Context:
         """True / False / "AUTO" (the library default)."""
         m = 2 if mode == "AUTO" else (1 if mode else 0)
         _check(lib().fskmc_set_cell_grouping(self.h, m), self.h)
+
+    def set_edge_screen(self, on: bool):
+        """Binary64 clock: screened window-edge decisions (True, the default)
+        or every decision from the binary64 divide (False)."""
+        _check(lib().fskmc_set_edge_screen(self.h, 1 if on else 0), self.h)
 
     def set_spin_limit(self, polls: int):
         _check(lib().fskmc_set_spin_limit(self.h, polls), self.h)

@@ -42,6 +42,7 @@ struct fskmc_ctx {
     fskmc_engine engine = FSKMC_ENGINE_PLAIN;
     int wpb = 2;
     int grouping = 2;      // several small cells per warp: 0 off, 1 on, 2 auto (spin-flip models)
+    int edge_screen = 1;   // binary64 clock: screened window-edge decisions
     uint32_t spin_limit = 1u << 20;
     fskmc_task_order order = FSKMC_ORDER_AUTO;
     int nsm = 152;                       // SMs of the context's device
@@ -462,6 +463,7 @@ fskmc_status plain_window(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         a.packed = c->packed ? 1 : 0;
         a.order = nullptr;
         a.lanes_per_cell = lanes;
+        a.screen = c->edge_screen;
         const Replica &R = c->reps[r];
         int nactive = R.ncx * R.ncy / 2;
         if (ordered) a.order = c->d_order + R.cell_off + (size_t)win.colour * nactive;
@@ -505,6 +507,7 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
         pr.spin_limit = c->spin_limit;
         pr.packed = c->packed;
         pr.lanes_per_cell = lanes_per_cell(c);
+        pr.screen = c->edge_screen != 0;
         pr.order = nullptr;
         if (use_order(c, c->total_cells / 2, true)) {
             fskmc_status st = build_order(c, 0, c->nrep, 0, 1);
@@ -638,6 +641,14 @@ fskmc_status fskmc_set_cell_grouping(fskmc_ctx *c, int32_t on)
     if (!c) return FSKMC_EINVAL;
     if (on < 0 || on > 2) return fail(c, FSKMC_EINVAL, "cell grouping must be 0 (off), 1 (on) or 2 (auto)");
     c->grouping = on;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_edge_screen(fskmc_ctx *c, int32_t on)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (on != 0 && on != 1) return fail(c, FSKMC_EINVAL, "edge screen must be 0 (off) or 1 (on)");
+    c->edge_screen = on;
     return FSKMC_OK;
 }
 

@@ -359,6 +359,48 @@ __device__ __forceinline__ uint8_t ld_site(const uint8_t *p)
     return *p;
 }
 
+// Screened window-edge check of the binary64 clock (Eq. skeleton: is
+// end = tau + (-log u_t) / lambda past the window length h?). The waiting
+// time is estimated in binary32 -- lf = -log u_t rounded toward zero, over
+// lambda truncated to binary32, a reciprocal within one unit in the last
+// place, three rounded products: at most 4.5 2^-23 relative error -- in
+// units of h 2^-62 (sf = 2^62 / h in binary32) and added to an exact 64-bit
+// integer clock clk. err bounds the distance of clk from the binary64 clock:
+// 2^-20 of each estimate, plus 2^11 units per event for the truncation to an
+// integer and the binary64 roundings of tau (at most 2^-52 h, i.e. 2^10
+// units, each). Q and E are the event's estimate and the bound with it.
+// take: clk + Q + E < 2^62, so the binary64 end lies before h; unsure:
+// neither that nor clk + Q >= 2^62 + E (the binary64 end at or past h), or
+// lambda outside the binary32 range, or screening off (ok false), or
+// `near`: the caller then decides in binary64.
+__device__ __forceinline__ void edge_screen(float lf, double lam, float sf, uint64_t clk, uint64_t err,
+                                            bool ok, bool near, uint64_t &Q, uint64_t &E, bool &take,
+                                            bool &unsure)
+{
+    const uint64_t lb = (uint64_t)dbits(lam);
+    const int fe = (int)(lb >> 52) - 896;  // binary32 exponent field of lambda
+    const bool inrange = ok && fe >= 1 && fe <= 250;
+    const float lamf = __uint_as_float(((uint32_t)fe << 23) | (uint32_t)((lb >> 29) & 0x7FFFFFu));
+    float rr;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(lamf));
+    const uint32_t qb = __float_as_uint(__fmul_rn(__fmul_rn(lf, rr), sf));
+    const int qe = (int)(qb >> 23) - 150;  // estimate = (24-bit significand) 2^qe
+    const uint64_t qm = (uint64_t)((qb & 0x7FFFFFu) | 0x800000u);
+    Q = qe >= 40 ? (1ull << 63) : (qe >= 0 ? qm << qe : (qe > -24 ? qm >> -qe : 0ull));
+    E = err + (Q >> 20) + 2048ull;
+    const uint64_t rem = (1ull << 62) - clk;
+    take = inrange && Q + E < rem;
+    unsure = near || !inrange || (!take && Q < rem + E);
+}
+
+// binary32 2^62 / h for the screened edge check, and whether h is in its range
+__device__ __forceinline__ bool edge_screen_scale(double h, bool on, float &sf)
+{
+    const bool ok = on && h > 1e-15 && h < 1e15;
+    sf = ok ? (float)(0x1p62 / h) : 0.0f;
+    return ok;
+}
+
 struct PParams {
     const Replica *reps;
     int32_t nrep;
@@ -373,6 +415,7 @@ struct PParams {
     const int2 *prev;          // per (replica,) window: last earlier window of the same / other colour
     const int32_t *order;      // per replica and colour: active cells heaviest first, or null
     int32_t inplace;           // in-place models: only active cells have tasks
+    int32_t screen;            // binary64 clock: screened window-edge decisions
     const double *h;
     int64_t nwin;
     uint32_t w0;

@@ -79,7 +79,7 @@ __host__ __device__ inline GLayout make_glayout(int qx, int qy, int W)
 // runs), and owns membership word l for the rank search.
 template <int MODEL, typename CLK, bool PERSIST, bool PACKED, int W>
 __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, const CellGeom &G,
-                             bool valid, int cx, int cy, uint32_t w, double hwin, uint64_t seed,
+                             bool valid, int cx, int cy, uint32_t w, double hwin, bool screen, uint64_t seed,
                              const uint8_t *src, uint8_t *dst, int lane, uint32_t *ev_out,
                              bool *amb_out, bool *bad_out, uint32_t *nexact_out)
 {
@@ -200,13 +200,14 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     // each batch of W events, lane i divides event i's l by its lambda for
     // the batch just ended, and iteration i of the next batch adds that
     // waiting time to tau, in event order. An event the estimate cannot
-    // decide (an end within about 2^-20 h of the edge, or lambda outside
-    // the binary32 range; about one per thousand cell-windows) catches up a
+    // decide (an end within about 2^-20 h of the edge, lambda outside the
+    // binary32 range, or screening off; about one per thousand cell-windows
+    // at 16x16 Ising cells and 369 events per window) catches up a
     // copy of tau and decides in binary64 on the spot; once such an event is
     // taken, so are the group's remaining decisions of the window (the
     // integer clock may then stand past 2^62).
-    const bool screen_ok = hwin > 1e-15 && hwin < 1e15;
-    const float sf = screen_ok ? (float)(0x1p62 / hwin) : 0.0f;
+    float sf;
+    const bool screen_ok = edge_screen_scale(hwin, screen, sf);
     uint64_t clk = 0, err = 0;
     double lam_mine = 1.0, lq_prev = 0.0;  // lane i: event i of the batch
     int ntaken_cur = 0, ntaken_prev = 0;   // events taken in this batch, in the previous one
@@ -317,20 +318,7 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             if (gl == sl) lam_mine = lamd;
             const double uc = __shfl_sync(FULL, ruc, sl, W);
             const float lf = __shfl_sync(FULL, rlf, sl, W);
-            const uint64_t lb = (uint64_t)dbits(lamd);
-            const int fe = (int)(lb >> 52) - 896;  // binary32 exponent field of lambda
-            const bool inrange = screen_ok && fe >= 1 && fe <= 250;
-            const float lamf = __uint_as_float(((uint32_t)fe << 23) | (uint32_t)((lb >> 29) & 0x7FFFFFu));
-            float rr;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(lamf));
-            const uint32_t qb = __float_as_uint(__fmul_rn(__fmul_rn(lf, rr), sf));
-            const int qe = (int)(qb >> 23) - 150;  // estimate = (24-bit significand) 2^qe
-            const uint64_t qm = (uint64_t)((qb & 0x7FFFFFu) | 0x800000u);
-            Qs = qe >= 40 ? (1ull << 63) : (qe >= 0 ? qm << qe : (qe > -24 ? qm >> -qe : 0ull));
-            Es = err + (Qs >> 20) + 2048ull;
-            const uint64_t rem = (1ull << 62) - clk;
-            take = inrange && Qs + Es < rem;
-            unsure = near_edge || !inrange || (!take && Qs < rem + Es);
+            edge_screen(lf, lamd, sf, clk, err, screen_ok, near_edge, Qs, Es, take, unsure);
             if (PERSIST) {
                 if (!take && !unsure) act = false;  // the event lies past the edge
                 if (!__any_sync(FULL, act)) break;
@@ -530,7 +518,7 @@ __global__ void __launch_bounds__(256) fs_group_kernel(WindowArgs a, int nactive
     uint32_t ev;
     uint32_t nexact;
     bool amb, bad;
-    group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cx, cy, a.w, a.h, a.seed,
+    group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cx, cy, a.w, a.h, a.screen != 0, a.seed,
                                                 a.src + R.lat_off, a.dst + R.lat_off, lane, &ev,
                                                 &amb, &bad, &nexact);
     if (valid && (lane & (W - 1)) == 0) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)ev;
@@ -618,7 +606,7 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
         uint32_t nexact;
         bool amb, bad;
         group_window<MODEL, CLK, true, PACKED, W>(csm, Lo, R, P.geom, valid, cx, cy, P.w0 + (uint32_t)i,
-                                                   P.h[i], P.seed, cur, cur, lane, &ev, &amb, &bad,
+                                                   P.h[i], P.screen != 0, P.seed, cur, cur, lane, &ev, &amb, &bad,
                                                    &nexact);
         if (valid && gl == 0) P.workload[R.cell_off + m] = (int32_t)ev;
         add_counters<W>(P.counters, lane, valid, ev, amb, bad, nexact);

@@ -69,6 +69,7 @@ struct WindowArgs {
     int32_t packed;            // lattice stored 1 bit per site (spin-flip models)
     const int32_t *order;      // active cells of the window (cell ids) in issue order, or null
     int32_t lanes_per_cell;    // 32: one cell per warp; 4, 8 or 16: grouped (spin-flip models)
+    int32_t screen;            // binary64 clock: screened window-edge decisions (edge_screen)
 };
 
 // Shared-memory bytes one warp of the window kernel needs.

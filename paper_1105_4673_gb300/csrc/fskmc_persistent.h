@@ -29,6 +29,7 @@ struct PersistentRun {
     const int32_t *order;         // device: active cells per replica and colour, heaviest
                                   // first (see launch_order), or null for row-major order
     int lanes_per_cell;           // 32, or the width of the grouped kernel (spin-flip models)
+    bool screen;                  // binary64 clock: screened window-edge decisions
 };
 
 struct PersistentState;  // device buffers and the captured CUDA graph

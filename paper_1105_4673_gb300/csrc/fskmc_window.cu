@@ -146,9 +146,9 @@ __device__ void copy_unwritten(const uint8_t *src, uint8_t *dst, int lx, int ly,
 // (lambda, waiting time, tau) is binary32 relative to the window start.
 template <int MODEL, typename CLK, bool PERSIST, bool PACKED>
 __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &G, int cx, int cy,
-                                int colour, uint32_t w, double hwin, uint64_t seed,
+                                int colour, uint32_t w, double hwin, bool screen, uint64_t seed,
                                 const uint8_t *src, uint8_t *dst, int lane, bool *amb_out,
-                                bool *bad_out)
+                                bool *bad_out, uint32_t *nexact_out)
 {
     using TR = Traits<MODEL>;
     constexpr bool F64 = sizeof(CLK) == 8;
@@ -403,6 +403,25 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     float rlf = 0.0f;
     uint32_t rw2 = 0;
     const uint32_t ctr3 = R.rep | (TAG_EVENT << 24);
+    // Binary64 clock, plain kernel: window-edge decisions screened by a
+    // binary32 estimate on an exact integer clock (edge_screen); the binary64
+    // clock tau runs one draw batch (32 events) behind -- at each batch start
+    // lane i divides event i's l by its lambda for the batch just ended, and
+    // event i of the next batch adds that waiting time to tau, in event order
+    // -- and decides the events the estimate cannot, after catching up a copy
+    // of tau; once such an event is taken the window's remaining decisions
+    // are taken the same way (with the screen off or a window length outside
+    // its range: every decision). The persistent kernel, bound by issue and
+    // occupancy, where the screen's registers cost more than its latency
+    // saves, divides and adds in binary64 for every event before its class
+    // choice.
+    float sf = 0.0f;
+    const bool screen_ok = !PERSIST && edge_screen_scale(hwin, screen, sf);
+    uint64_t clk = 0, err = 0;
+    double lam_mine = 1.0, lq_prev = 0.0;  // lane i: event i of the batch
+    int ntaken_cur = 0, ntaken_prev = 0;   // events taken in this batch, in the previous one
+    uint32_t nexact = 0;
+    bool near_edge = false;
 
     for (;;) {
         // Counts of this state, one class per lane.
@@ -436,12 +455,20 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             break;
         }
         if ((e & 31u) == 0u) {
+            if (F64 && !PERSIST) {
+                // binary64 waiting times of the batch just ended, one event per lane
+                const bool mine = lane < ntaken_cur;
+                lq_prev = div_rn(mine ? rl : 1.0, mine ? lam_mine : 1.0);
+                ntaken_prev = ntaken_cur;
+                ntaken_cur = 0;
+            }
             // 32 events' draws at once, one Philox block per lane
             u32x4 o = draw(seed, e + (uint32_t)lane, w, (uint32_t)m, ctr3);
             if (F64) {
                 uint64_t b = ((uint64_t)o.x << 21) | (uint64_t)(o.y >> 11);
                 rl = neg_log_u53(b + 1ull);
                 ruc = u53_scaled(2ull * o.z + 1ull, 33);  // (o.z + 1/2) 2^-32
+                if (!PERSIST) rlf = __double2float_rz(rl);
             } else {
                 rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
             }
@@ -451,12 +478,13 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         const int src_lane = (int)(e & 31u);
         const uint32_t w3 = __shfl_sync(0xffffffffu, rw3, src_lane);
         int k;
-        if (F64) {
+        if (F64 && PERSIST) {
             const double l = __shfl_sync(0xffffffffu, rl, src_lane);
             const double uc = __shfl_sync(0xffffffffu, ruc, src_lane);
             const double end = __dadd_rn(tau, div_rn(l, lamd));
             const long long eb = dbits(end);
             if (llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+            ++nexact;
             if (eb >= hbits) break;
             tau = end;
             const long long tb = dbits(__dmul_rn(uc, lamd));
@@ -464,6 +492,48 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
 #pragma unroll
             for (int kk = K - 2; kk >= 0; --kk)
                 if (tb < dbits(Pd[kk])) k = kk;
+        } else if (F64) {
+            {  // the binary64 clock, one batch behind
+                const double v = __shfl_sync(0xffffffffu, lq_prev, src_lane);
+                if (src_lane < ntaken_prev) tau = __dadd_rn(tau, v);
+            }
+            if (lane == src_lane) lam_mine = lamd;
+            const double uc = __shfl_sync(0xffffffffu, ruc, src_lane);
+            const float lf = __shfl_sync(0xffffffffu, rlf, src_lane);
+            uint64_t Qs, Es;
+            bool take, unsure;
+            edge_screen(lf, lamd, sf, clk, err, screen_ok, near_edge, Qs, Es, take, unsure);
+            const long long tb = dbits(__dmul_rn(uc, lamd));
+            k = K - 1;
+#pragma unroll
+            for (int kk = K - 2; kk >= 0; --kk)
+                if (tb < dbits(Pd[kk])) k = kk;
+            if (unsure) {
+                // binary64 decision: tau up to event e - 1 (the rest of the
+                // previous batch, then this batch's events before e, all
+                // taken), plus event e's waiting time
+                double t = tau;
+                for (int i = 1; i < 32; ++i) {
+                    const double v = __shfl_sync(0xffffffffu, lq_prev, i);
+                    if (i > src_lane && i < ntaken_prev) t = __dadd_rn(t, v);
+                }
+                const bool mine = lane <= src_lane;
+                const double lqc = div_rn(mine ? rl : 1.0, mine ? lam_mine : 1.0);
+                for (int i = 0; i < 31; ++i) {
+                    const double v = __shfl_sync(0xffffffffu, lqc, i);
+                    if (i < src_lane) t = __dadd_rn(t, v);
+                }
+                const double end = __dadd_rn(t, __shfl_sync(0xffffffffu, lqc, src_lane));
+                const long long eb = dbits(end);
+                if (llabs(eb - hbits) < 9008ll) amb = true;  // |end - h| below ~1e-12 h
+                take = eb < hbits;
+                near_edge = true;
+                ++nexact;
+            }
+            if (!take) break;
+            clk += Qs;
+            err = Es;
+            ++ntaken_cur;
         } else {
             const float l = __shfl_sync(0xffffffffu, rlf, src_lane);
             const uint32_t w2 = __shfl_sync(0xffffffffu, rw2, src_lane);
@@ -763,6 +833,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
         }
     }
     *amb_out = amb;
+    *nexact_out = nexact;
     return e;
 }
 
@@ -796,14 +867,16 @@ __global__ void __launch_bounds__(512) fs_window_kernel(WindowArgs a, int nactiv
         copy_unwritten<false>(src, dst, R.lx, R.ly, a.geom.qx, a.geom.qy, ncx2, ncy2, a.colour, lane);
     }
     bool amb = false, bad = false;
+    uint32_t nexact = 0;
     uint32_t e = cell_window<MODEL, CLK, false, PACKED>(smem + (size_t)wib * smem_per_warp, R, a.geom, cx,
-                                                cy, a.colour, a.w, a.h, a.seed, src, dst, lane,
-                                                &amb, &bad);
+                                                cy, a.colour, a.w, a.h, a.screen != 0, a.seed, src, dst,
+                                                lane, &amb, &bad, &nexact);
     if (lane == 0) {
         a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
         atomicAdd(&a.counters[0], (unsigned long long)e);
         if (amb) atomicAdd(&a.counters[1], 1ull);
         if (bad) atomicAdd(&a.counters[3], 1ull);
+        if (nexact) atomicAdd(&a.counters[4], (unsigned long long)nexact);
     }
 }
 
@@ -904,14 +977,16 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         if (!ok) break;
         if (active) {
             bool amb = false, bad = false;
+            uint32_t nexact = 0;
             uint32_t e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cx, cy, ccol,
-                                                      P.w0 + (uint32_t)i, P.h[i], P.seed, cur,
-                                                      nxt, lane, &amb, &bad);
+                                                      P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
+                                                      cur, nxt, lane, &amb, &bad, &nexact);
             if (lane == 0) {
                 P.workload[R.cell_off + m] = (int32_t)e;
                 atomicAdd(&P.counters[0], (unsigned long long)e);
                 if (amb) atomicAdd(&P.counters[1], 1ull);
                 if (bad) atomicAdd(&P.counters[3], 1ull);
+                if (nexact) atomicAdd(&P.counters[4], (unsigned long long)nexact);
             }
         } else {
             copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.geom.qx, P.geom.qy, cx, cy, wcol, lane);
@@ -1151,6 +1226,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     P.prev = st->d_prev;
     P.order = run.order;
     P.inplace = run.lat2 == nullptr ? 1 : 0;
+    P.screen = run.screen ? 1 : 0;
     P.h = st->d_h;
     P.nwin = run.nwin;
     P.w0 = (uint32_t)run.w0;

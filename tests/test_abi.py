@@ -73,6 +73,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.fskmc_sync(None) == F.EINVAL
     assert lib.fskmc_stats(None, None) == F.EINVAL
     assert lib.fskmc_exact_edge_checks(None, None) == F.EINVAL
+    assert lib.fskmc_set_edge_screen(None, 1) == F.EINVAL
     lib.fskmc_destroy(None)
 
 

@@ -171,43 +171,55 @@ def test_grouping_switch_rejects_bad_values():
 # High rates (about 10^4 events per cell-window), so that a few percent of
 # the cell-windows end within the screened edge check's error bound and take
 # that decision from the binary64 clock; and a window too long for the
-# screen (every decision in binary64).
+# screen (every decision in binary64). The two-site models run one cell per
+# warp.
 SCREEN_CASES = [
     ("ADSDES", 1024, 512, (32, 16), dict(ka=40.0, kd=40.0, betaJ=0.5), 1.0),
     ("ISING", 1024, 512, (16, 16), dict(ka=40.0, kd=40.0, betaJ=0.3), 1.0),
     ("ISING1D", 65536, 1, (128, 1), dict(ka=40.0, kd=40.0, betaJ=1.0, betah=0.5), 1.0),
     ("ADSDES", 256, 128, (8, 8), dict(ka=1e-16, kd=1e-16, betaJ=0.5), 2e15),
+    ("ZGB", 512, 512, (32, 32), dict(yA=0.5, kr=50.0, kd=5.0), 4.0),
+    ("DIFFUSION", 512, 512, (32, 32), dict(ka=4.0, kd=4.0, betaJ=0.5, nu=20.0), 1.0),
 ]
 
 
 @pytest.mark.parametrize("model,lx,ly,q,rates,dt", SCREEN_CASES)
 @pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
 def test_screened_edge_check_matches_binary64(model, lx, ly, q, rates, dt, engine):
-    """The grouped binary64 kernels decide window edges from a bounded
-    binary32 estimate and fall back to the binary64 clock for decisions
-    inside the bound: lattices, events and workloads equal those of the
-    one-cell kernels, which always divide in binary64."""
+    """Binary64 window-edge decisions screened by a bounded binary32
+    estimate, with the binary64 clock deciding the events inside the bound:
+    lattices, events, workloads and ambiguity counts equal those of every
+    decision taken from the binary64 divide, in the grouped and the one-cell
+    kernels."""
     seed = 0x5C + lx
     init = oracle.init_bernoulli(lx, ly, seed, 0.5)
-    res = []
-    for grouped in (True, False):
+    if model == "ZGB":
+        init = np.zeros_like(init)  # an empty surface
+    spin = model in ("ADSDES", "ISING", "ISING1D")
+    forms = [(g, sc) for g in ((True, False) if spin else (False,)) for sc in (True, False)]
+    res = {}
+    for grouped, screen in forms:
         with F.Context(lx, ly, model, rates, q) as c:
             c.set_engine(engine)
             c.set_cell_grouping(grouped)
+            c.set_edge_screen(screen)
             c.set_state(init)
             c.run("LIE", dt, 4.0 * dt, seed)
-            res.append((c.get_state(), c.stats(), c.workload(), c.info()["lanes_per_cell"]))
-    (la, sa, wa, wda), (lb, sb, wb, wdb) = res
-    assert wda < 32 and wdb == 32
-    assert sa["exact_edge_checks"] > 0 and sb["exact_edge_checks"] == 0
-    if dt > 1e15:  # beyond the screen's range: every decision in binary64
-        assert sa["exact_edge_checks"] >= sa["events"] > 0
-    else:
-        assert sa["exact_edge_checks"] < sa["events"] // 1000
-    assert sa["check_failures"] == 0 and sa["timeouts"] == 0
-    assert sa["events"] == sb["events"] and sa["ambiguous"] == sb["ambiguous"]
-    assert np.array_equal(la, lb)
-    assert np.array_equal(wa, wb)
+            res[grouped, screen] = (c.get_state(), c.stats(), c.workload(), c.info()["lanes_per_cell"])
+    lr, sr, wr, _ = res[False, False]
+    assert sr["events"] > 0 and sr["exact_edge_checks"] >= sr["events"]  # every decision in binary64
+    for (grouped, screen), (la, sa, wa, lanes) in res.items():
+        assert (lanes < 32) == grouped
+        assert sa["check_failures"] == 0 and sa["timeouts"] == 0
+        assert sa["events"] == sr["events"] and sa["ambiguous"] == sr["ambiguous"], (grouped, screen)
+        assert np.array_equal(la, lr), (grouped, screen)
+        assert np.array_equal(wa, wr), (grouped, screen)
+        if not screen or dt > 1e15 or (engine == "PERSISTENT" and not grouped):
+            # screen off, beyond its range, or the persistent one-cell kernel
+            # (never screened): every decision in binary64
+            assert sa["exact_edge_checks"] >= sa["events"]
+        else:
+            assert 0 < sa["exact_edge_checks"] < sa["events"] // 1000, (grouped, sa["exact_edge_checks"])
 
 
 @pytest.mark.parametrize("model,rates", [
