@@ -110,45 +110,78 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     // Stage the cell and its halo (periodic wrap) from the window-start
     // state; on the ring only the cell's own row.
     if (valid) {
-        // walk the box in row-major steps of W without dividing by its width
+        // walk the box in row-major steps of W without dividing by its width,
+        // UB loads in flight per lane before their stores
+        constexpr int UB = 8;
+        const int total = ring ? BW : BW * BH;
         int by = ring ? HW : 0, bx = gl;
         while (bx >= BW) { bx -= BW; ++by; }
-        for (int i = gl; i < (ring ? BW : BW * BH); i += W) {
-            int gy = Y0 - HW + by, gx = X0 - HW + bx;
-            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-            gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
-            const int bi = by * BW + bx;
-            if (PACKED) {
-                const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
-                const uint32_t wv = PERSIST ? __ldcg(w32) : *w32;
-                box[bi] = (uint8_t)((wv >> (gx & 31)) & 1u);
-            } else {
-                box[bi] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+        for (int i0 = gl; i0 < total; i0 += UB * W) {
+            uint32_t v[UB];
+            int bi[UB], sh[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                bi[u] = -1;
+                v[u] = 0u;
+                sh[u] = 0;
+                if (i0 + u * W < total) {
+                    int gy = Y0 - HW + by, gx = X0 - HW + bx;
+                    gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+                    gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+                    bi[u] = by * BW + bx;
+                    if (PACKED) {
+                        const uint32_t *w32 = reinterpret_cast<const uint32_t *>(src) + (int64_t)gy * (lx >> 5) + (gx >> 5);
+                        v[u] = PERSIST ? __ldcg(w32) : *w32;
+                        sh[u] = gx & 31;
+                    } else {
+                        v[u] = ld_site<PERSIST>(src + (int64_t)gy * lx + gx);
+                    }
+                }
+                bx += W;
+                while (bx >= BW) { bx -= BW; ++by; }
             }
-            bx += W;
-            while (bx >= BW) { bx -= BW; ++by; }
+#pragma unroll
+            for (int u = 0; u < UB; ++u)
+                if (bi[u] >= 0) box[bi[u]] = (uint8_t)(PACKED ? (v[u] >> sh[u]) & 1u : v[u]);
         }
     }
     for (int i = gl; i < MAX_CLASSES; i += W) cnt[i] = 0;  // a cell-less group keeps zero rates
     __syncwarp();
 
     // Class build: lane gl classifies its run of 32 sites (word gl; words
-    // past the cell's last site are zero).
+    // past the cell's last site are zero). The class of a site is
+    // SK sigma + n (n = occupied neighbours: 4 in 2D, 2 on the ring; the
+    // states are 0/1, so n is the sum of the neighbours' bytes); the lane
+    // gathers sigma and the three bits of n as bit planes over its sites and
+    // forms each class's membership word from them.
     if (valid) {
-        uint32_t mk[TR::KS];
-#pragma unroll
-        for (int k = 0; k < TR::KS; ++k) mk[k] = 0u;
-        for (int t = 0; t < 32; ++t) {
-            const int i = gl * 32 + t;
-            if (i >= nsite) break;
-            const int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
-            const int k = site_class<MODEL>(box, BW, (lly + HW) * BW + llx + HW);
-            scls[i] = (uint8_t)k;
-#pragma unroll
-            for (int kk = 0; kk < TR::KS; ++kk) mk[kk] |= (uint32_t)(k == kk) << t;
+        uint32_t ps = 0u, p0 = 0u, p1 = 0u, p2 = 0u;
+        const int i0 = gl * 32;
+        const int nt = min(32, nsite - i0);  // sites of this word (none past the cell's last)
+        int lly = (int)fdiv((uint32_t)i0, G.fqx), llx = i0 - lly * qx;
+#pragma unroll 4
+        for (int t = 0; t < nt; ++t) {
+            const int p = (lly + HW) * BW + llx + HW;
+            const uint32_t s = box[p];
+            const uint32_t n = ring ? (uint32_t)box[p - 1] + box[p + 1]
+                                    : (uint32_t)box[p - BW] + box[p + BW] + box[p - 1] + box[p + 1];
+            scls[i0 + t] = (uint8_t)(SK * s + n);
+            ps |= s << t;
+            p0 |= (n & 1u) << t;
+            p1 |= ((n >> 1) & 1u) << t;
+            p2 |= (n >> 2) << t;
+            if (++llx == qx) { llx = 0; ++lly; }
         }
+        const uint32_t vm = nt >= 32 ? 0xffffffffu : (nt > 0 ? (1u << nt) - 1u : 0u);
 #pragma unroll
-        for (int k = 0; k < TR::KS; ++k) mask[k * W + gl] = mk[k];
+        for (int kk = 0; kk < TR::KS; ++kk) {
+            const int sg = kk / SK, v = kk % SK;
+            uint32_t mk = vm & (sg ? ps : ~ps);
+            mk &= (v & 1) ? p0 : ~p0;
+            mk &= (v & 2) ? p1 : ~p1;
+            mk &= (v & 4) ? p2 : ~p2;
+            mask[kk * W + gl] = mk;
+        }
     }
     __syncwarp();
     if (valid) {
@@ -456,9 +489,12 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
                 }
             }
         } else {
+            int lly = (int)fdiv((uint32_t)gl, G.fqx), llx = gl - lly * qx;
+#pragma unroll 4
             for (int i = gl; i < nsite; i += W) {
-                const int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
                 dst[(int64_t)(Y0 + lly) * lx + X0 + llx] = box[(lly + HW) * BW + llx + HW];
+                llx += W;
+                while (llx >= qx) { llx -= qx; ++lly; }
             }
         }
     }
