@@ -109,7 +109,57 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
 
     // Stage the cell and its halo (periodic wrap) from the window-start
     // state; on the ring only the cell's own row.
-    if (valid) {
+    const bool rows16 = !PACKED && (qx & 15) == 0 && (lx & 15) == 0;
+    if (valid && rows16) {
+        // byte lattice, cell width a multiple of 16: each box row is qx/16
+        // aligned 16-byte chunks of the cell's row plus its two halo sites;
+        // items (row, chunk or halo) in row-major steps of W, UB16 loads in
+        // flight per lane before their stores
+        constexpr int UB16 = F64 ? 8 : 2;  // the binary32 kernels keep their registers low (occupancy)
+        const int nch = qx >> 4, per_row = nch + 2;
+        const int total = (ring ? 1 : BH) * per_row;
+        int by = ring ? HW : 0, c = gl;
+        while (c >= per_row) { c -= per_row; ++by; }
+        for (int i0 = gl; i0 < total; i0 += UB16 * W) {
+            uint4 v[UB16];
+            int bi[UB16], kind[UB16];
+#pragma unroll
+            for (int u = 0; u < UB16; ++u) {
+                kind[u] = -1;  // -1 none, 0 chunk, 1 halo site
+                bi[u] = 0;
+                v[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (i0 + u * W < total) {
+                    int gy = Y0 - HW + by;
+                    gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+                    const uint8_t *row = src + (int64_t)gy * lx;
+                    if (c < nch) {
+                        const uint4 *p16 = reinterpret_cast<const uint4 *>(row + X0 + 16 * c);
+                        v[u] = PERSIST ? __ldcg(p16) : *p16;
+                        bi[u] = by * BW + HW + 16 * c;
+                        kind[u] = 0;
+                    } else {
+                        int gx = c == nch ? X0 - 1 : X0 + qx;
+                        gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
+                        v[u].x = ld_site<PERSIST>(row + gx);
+                        bi[u] = by * BW + (c == nch ? 0 : HW + qx);
+                        kind[u] = 1;
+                    }
+                }
+                c += W;
+                while (c >= per_row) { c -= per_row; ++by; }
+            }
+#pragma unroll
+            for (int u = 0; u < UB16; ++u) {
+                if (kind[u] == 0) {
+                    const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int b = 0; b < 16; ++b) box[bi[u] + b] = (uint8_t)(wv[b >> 2] >> (8 * (b & 3)));
+                } else if (kind[u] == 1) {
+                    box[bi[u]] = (uint8_t)v[u].x;
+                }
+            }
+        }
+    } else if (valid) {
         // walk the box in row-major steps of W without dividing by its width,
         // UB loads in flight per lane before their stores
         constexpr int UB = 8;
