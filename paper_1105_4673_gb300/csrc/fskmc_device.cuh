@@ -409,6 +409,7 @@ struct PParams {
     int32_t *workload;
     unsigned long long *counters;
     const int32_t *act_prefix;  // [nrep + 1] prefix sums of active cells per window
+    const int2 *cell_rk;        // [total_active]: replica and index within it of a window's a-th active cell
     int32_t total_cells, total_active;
     const int8_t *colour;
     int32_t colour_per_replica;

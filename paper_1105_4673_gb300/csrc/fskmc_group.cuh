@@ -646,13 +646,9 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
         const int u = ch * GC + lane / W;
         const bool valid = u < per_window;
         const int a = valid ? u : ch * GC;  // a cell-less group borrows the chunk's first cell's replica
-        int lo = 0, hi = P.nrep;            // last r with act_prefix[r] <= a
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (P.act_prefix[mid] <= a) lo = mid; else hi = mid;
-        }
-        const int r = lo;
-        const int k = a - P.act_prefix[r];
+        const int2 rk = P.cell_rk[a];
+        const int r = rk.x;
+        const int k = rk.y;
         const Replica &R = P.reps[r];
         const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
         const int ccol = P.colour[widx];

@@ -912,11 +912,24 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
     const int per_window = inplace ? P.total_active : P.total_cells;
     const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)per_window;
 
+    // In-place models: the next task is dequeued while this one runs, which
+    // hides the round trip to the much-contended queue counter (tasks wait
+    // only on tasks of earlier windows, all dequeued before it, so holding
+    // one cannot block them). The ping-pong model's dense copy tasks run
+    // better without it.
+    unsigned long long t_next = 0;
+    if (inplace && lane == 0) t_next = atomicAdd(P.queue, 1ull);
     for (;;) {
         unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(P.queue, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= total) break;
+        if (inplace) {
+            t = __shfl_sync(0xffffffffu, t_next, 0);
+            if (t >= total) break;
+            if (lane == 0) t_next = atomicAdd(P.queue, 1ull);
+        } else {
+            if (lane == 0) t = atomicAdd(P.queue, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= total) break;
+        }
         int ab = 0;
         if (lane == 0) ab = *(volatile int32_t *)P.abort_flag;
         if (__shfl_sync(0xffffffffu, ab, 0)) break;
@@ -924,13 +937,9 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
         const int u = (int)(t % (unsigned long long)per_window);
         const bool active = u < P.total_active;
         const int a = active ? u : u - P.total_active;
-        int lo = 0, hi = P.nrep;  // last r with act_prefix[r] <= a
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (P.act_prefix[mid] <= a) lo = mid; else hi = mid;
-        }
-        const int r = lo;
-        const int k = a - P.act_prefix[r];
+        const int2 rk = P.cell_rk[a];
+        const int r = rk.x;
+        const int k = rk.y;
         const Replica &R = P.reps[r];
         const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
         const int wcol = P.colour[widx];
@@ -1083,6 +1092,7 @@ struct PersistentState {
     int32_t *d_epoch = nullptr;
     unsigned long long *d_queue = nullptr;  // [0] queue, [1] abort flag (low word)
     int32_t *d_prefix = nullptr;
+    int2 *d_cell_rk = nullptr;
     int8_t *d_colour = nullptr;
     size_t colour_cap = 0;
     int2 *d_prev = nullptr;
@@ -1104,6 +1114,7 @@ void persistent_free(PersistentState *st)
     cudaFree(st->d_epoch);
     cudaFree(st->d_queue);
     cudaFree(st->d_prefix);
+    cudaFree(st->d_cell_rk);
     cudaFree(st->d_colour);
     cudaFree(st->d_prev);
     cudaFree(st->d_h);
@@ -1135,6 +1146,13 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
             pre[r + 1] = pre[r] + run.reps_host[r].ncx * run.reps_host[r].ncy / 2;
         PCK(cudaMemcpyAsync(st->d_prefix, pre.data(), sizeof(int32_t) * pre.size(),
                             cudaMemcpyHostToDevice, s));
+        // a -> (replica, index within it): one load per task instead of a search
+        std::vector<int2> rk((size_t)std::max(pre[run.nrep], 1));
+        for (int r = 0; r < run.nrep; ++r)
+            for (int k = 0; k < pre[r + 1] - pre[r]; ++k) rk[(size_t)pre[r] + k] = make_int2(r, k);
+        PCK(cudaMalloc(&st->d_cell_rk, sizeof(int2) * rk.size()));
+        PCK(cudaMemcpyAsync(st->d_cell_rk, rk.data(), sizeof(int2) * rk.size(), cudaMemcpyHostToDevice, s));
+        PCK(cudaStreamSynchronize(s));  // the host vectors go out of scope
         st->total_cells = run.total_cells;
     }
     // (Re)build the graph when the kernel variant or launch shape changes.
@@ -1219,6 +1237,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     P.workload = run.workload;
     P.counters = run.counters;
     P.act_prefix = st->d_prefix;
+    P.cell_rk = st->d_cell_rk;
     P.total_cells = run.total_cells;
     P.total_active = run.total_cells / 2;
     P.colour = st->d_colour;
