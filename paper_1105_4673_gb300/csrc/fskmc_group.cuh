@@ -634,24 +634,38 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
     const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)chunks;
 
     for (;;) {
+        // the dequeue and the abort flag in one round trip
         unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(P.queue, 1ull);
+        int ab = 0;
+        if (lane == 0) {
+            t = atomicAdd(P.queue, 1ull);
+            ab = *(volatile int32_t *)P.abort_flag;
+        }
         t = __shfl_sync(FULL, t, 0);
         if (t >= total) break;
-        int ab = 0;
-        if (lane == 0) ab = *(volatile int32_t *)P.abort_flag;
         if (__shfl_sync(FULL, ab, 0)) break;
         const int i = (int)(t / (unsigned long long)chunks);
         const int ch = (int)(t % (unsigned long long)chunks);
         const int u = ch * GC + lane / W;
         const bool valid = u < per_window;
         const int a = valid ? u : ch * GC;  // a cell-less group borrows the chunk's first cell's replica
+        // one schedule for all replicas: the window's colour and dependencies
+        // load beside the cell's replica
+        int ccol = 0;
+        int2 pv = make_int2(0, 0);
+        if (!P.colour_per_replica) {
+            ccol = P.colour[i];
+            pv = P.prev[i];
+        }
         const int2 rk = P.cell_rk[a];
         const int r = rk.x;
         const int k = rk.y;
         const Replica &R = P.reps[r];
         const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
-        const int ccol = P.colour[widx];
+        if (P.colour_per_replica) {
+            ccol = P.colour[widx];
+            pv = P.prev[widx];
+        }
         int cx, cy;
         if (P.order) {
             const int mo = P.order[R.cell_off + ccol * ((R.ncx >> 1) * R.ncy) + k];
@@ -670,7 +684,6 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
         // neighbours' (E, S, W, N) last active window before this one. A ring
         // (one row of cells) has no vertical neighbours. Lane gl of a group
         // waits on dependencies gl, gl + W.
-        const int2 pv = P.prev[widx];
         bool ok = true;
 #pragma unroll
         for (int d0 = 0; d0 < 5; d0 += W) {
