@@ -143,8 +143,8 @@ FP64_DEP_LATENCY_CYCLES = 64
 # kernel source it was taken on.
 PROFILED_TRAFFIC = {
     "fs_group_kernel<ISING,double,packed,W=8>": {
-        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 181760,
-        "src_sha256": "2b4cd5c821ca1f39291359b7db7f466ef6abd502734be9783ac4d8a96c0e153b"},
+        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 186880,
+        "src_sha256": "dc064b1839fcca3bbe0fb6b48f183849800e685ec797d342a8c0ee7b42bf93f8"},
 }
 
 
