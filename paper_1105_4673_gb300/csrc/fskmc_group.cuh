@@ -161,8 +161,9 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         }
     } else if (valid) {
         // walk the box in row-major steps of W without dividing by its width,
-        // UB loads in flight per lane before their stores
-        constexpr int UB = 8;
+        // UB loads in flight per lane before their stores (fewer in the
+        // binary32 kernels, which keep their registers low)
+        constexpr int UB = F64 ? 8 : 4;
         const int total = ring ? BW : BW * BH;
         int by = ring ? HW : 0, bx = gl;
         while (bx >= BW) { bx -= BW; ++by; }

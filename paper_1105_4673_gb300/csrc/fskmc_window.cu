@@ -912,16 +912,18 @@ __global__ void __launch_bounds__(256) fs_persistent_kernel(const PParams *pp, i
     const int per_window = inplace ? P.total_active : P.total_cells;
     const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)per_window;
 
-    // In-place models: the next task is dequeued while this one runs, which
-    // hides the round trip to the much-contended queue counter (tasks wait
-    // only on tasks of earlier windows, all dequeued before it, so holding
-    // one cannot block them). The ping-pong model's dense copy tasks run
+    // In-place models with the binary64 clock: the next task is dequeued
+    // while this one runs, which hides the round trip to the much-contended
+    // queue counter (tasks wait only on tasks of earlier windows, all
+    // dequeued before it, so holding one cannot block them). The binary32
+    // clock's shorter tasks and the ping-pong model's dense copy tasks run
     // better without it.
+    const bool prefetch = inplace && sizeof(CLK) == 8;
     unsigned long long t_next = 0;
-    if (inplace && lane == 0) t_next = atomicAdd(P.queue, 1ull);
+    if (prefetch && lane == 0) t_next = atomicAdd(P.queue, 1ull);
     for (;;) {
         unsigned long long t = 0;
-        if (inplace) {
+        if (prefetch) {
             t = __shfl_sync(0xffffffffu, t_next, 0);
             if (t >= total) break;
             if (lane == 0) t_next = atomicAdd(P.queue, 1ull);
