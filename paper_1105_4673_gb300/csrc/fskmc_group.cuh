@@ -539,6 +539,23 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
                     atomicOr(drow + wi, bits);
                 }
             }
+        } else if (rows16) {
+            // aligned 16-byte chunks of the cell's rows
+            const int nch = qx >> 4;
+            int row = 0, c = gl;
+            while (c >= nch) { c -= nch; ++row; }
+            for (int t = gl; t < qy * nch; t += W) {
+                const uint8_t *b = box + (row + HW) * BW + HW + 16 * c;
+                uint32_t wv[4];
+#pragma unroll
+                for (int q4 = 0; q4 < 4; ++q4)
+                    wv[q4] = (uint32_t)b[4 * q4] | ((uint32_t)b[4 * q4 + 1] << 8) |
+                             ((uint32_t)b[4 * q4 + 2] << 16) | ((uint32_t)b[4 * q4 + 3] << 24);
+                *reinterpret_cast<uint4 *>(dst + (int64_t)(Y0 + row) * lx + X0 + 16 * c) =
+                    make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                c += W;
+                while (c >= nch) { c -= nch; ++row; }
+            }
         } else {
             int lly = (int)fdiv((uint32_t)gl, G.fqx), llx = gl - lly * qx;
 #pragma unroll 4

@@ -154,6 +154,8 @@ def test_grouping_switch_rejects_bad_values():
     with F.Context(64, 64, "ISING", RATES["ISING"], (8, 8)) as c:
         with pytest.raises(F.FskmcError):
             F._check(F.lib().fskmc_set_cell_grouping(c.h, 3), c.h)
+        with pytest.raises(F.FskmcError):
+            F._check(F.lib().fskmc_set_edge_screen(c.h, 2), c.h)
         assert c.info()["lanes_per_cell"] == 8  # auto: plain engine
         c.set_cell_grouping(False)
         assert c.info()["lanes_per_cell"] == 32
