@@ -143,8 +143,8 @@ FP64_DEP_LATENCY_CYCLES = 64
 # kernel source it was taken on.
 PROFILED_TRAFFIC = {
     "fs_group_kernel<ISING,double,packed,W=8>": {
-        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 186624,
-        "src_sha256": "c2d7232c30249a3f59aaa59500988e3f5fddcb93330825c5f6c92b5cadae9a68"},
+        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 186880,
+        "src_sha256": "196fdfa90747162fac54f84b80f0c113dcf7fbf75a77738ef23ecd32cccc9b96"},
 }
 
 
