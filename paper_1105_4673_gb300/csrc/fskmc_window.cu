@@ -174,36 +174,47 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     // ballots give each row's state masks for the bit-parallel class build.
     const bool zrow = (MODEL == ZGB) && !PACKED && qx == 32;
     const bool drow = (MODEL == DIFFUSION) && qx == 32;
-    if (drow) {
-        for (int by = 0; by < BH; ++by) {
-            int gy = Y0 - HW + by;
-            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-            const uint8_t *srow = src + (int64_t)gy * lx;
-            const uint8_t v = ld_site<PERSIST>(srow + X0 + lane);
-            box[by * BW + HW + lane] = v;
-            const uint32_t mo = __ballot_sync(0xffffffffu, v == 1);
-            if (lane == 0) rowm[by] = mo;
-            if (lane >= 1 && lane <= 4) {
-                // halo columns x = -2, -1, 32, 33
-                const int hx = lane <= 2 ? lane - 3 : 32 + (lane - 3);
-                int gx = X0 + hx;
-                gx += (gx < 0) ? lx : 0; gx -= (gx >= lx) ? lx : 0;
-                box[by * BW + HW + hx] = ld_site<PERSIST>(srow + gx);
+    if (drow || zrow) {
+        // UR rows' loads in flight (the row's 32 sites, one per lane, and its
+        // halo sites in a few lanes) before their stores and ballots
+        constexpr int UR = 8;
+        // diffusion: halo columns x = -2, -1, 32, 33 in lanes 1..4; ZGB:
+        // x = -1 in lane 1, x = 32 in lane 2
+        const int hx = drow ? (lane <= 2 ? lane - 3 : 32 + (lane - 3)) : (lane == 1 ? -1 : 32);
+        const bool hl = drow ? (lane >= 1 && lane <= 4) : (lane == 1 || lane == 2);
+        int hgx = X0 + hx;
+        hgx += (hgx < 0) ? lx : 0; hgx -= (hgx >= lx) ? lx : 0;
+        for (int by0 = 0; by0 < BH; by0 += UR) {
+            uint32_t v[UR], hv[UR];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int by = by0 + u;
+                v[u] = 0u;
+                hv[u] = 0u;
+                if (by < BH) {
+                    int gy = Y0 - HW + by;
+                    gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+                    const uint8_t *srow = src + (int64_t)gy * lx;
+                    v[u] = ld_site<PERSIST>(srow + X0 + lane);
+                    if (hl) hv[u] = ld_site<PERSIST>(srow + hgx);
+                }
             }
-        }
-    } else if (zrow) {
-        for (int by = 0; by < BH; ++by) {
-            int gy = Y0 - HW + by;
-            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-            const uint8_t *srow = src + (int64_t)gy * lx;
-            const uint8_t v = ld_site<PERSIST>(srow + X0 + lane);
-            box[by * BW + HW + lane] = v;
-            const uint32_t me = __ballot_sync(0xffffffffu, v == 0);
-            const uint32_t ma = __ballot_sync(0xffffffffu, v == 1);
-            const uint32_t mb = __ballot_sync(0xffffffffu, v == 2);
-            if (lane == 0) { rowm[by] = me; rowm[BH + by] = ma; rowm[2 * BH + by] = mb; }
-            if (lane == 1) box[by * BW] = ld_site<PERSIST>(srow + (X0 == 0 ? lx - 1 : X0 - 1));
-            if (lane == 2) box[by * BW + BW - 1] = ld_site<PERSIST>(srow + (X0 + 32 == lx ? 0 : X0 + 32));
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int by = by0 + u;
+                if (by >= BH) break;
+                box[by * BW + HW + lane] = (uint8_t)v[u];
+                if (hl) box[by * BW + HW + hx] = (uint8_t)hv[u];
+                if (drow) {
+                    const uint32_t mo = __ballot_sync(0xffffffffu, v[u] == 1u);
+                    if (lane == 0) rowm[by] = mo;
+                } else {
+                    const uint32_t me = __ballot_sync(0xffffffffu, v[u] == 0u);
+                    const uint32_t ma = __ballot_sync(0xffffffffu, v[u] == 1u);
+                    const uint32_t mb = __ballot_sync(0xffffffffu, v[u] == 2u);
+                    if (lane == 0) { rowm[by] = me; rowm[BH + by] = ma; rowm[2 * BH + by] = mb; }
+                }
+            }
         }
     } else {
         // Stage the cell and its halo (periodic wrap) from the window-start
