@@ -94,9 +94,15 @@ typedef enum { FSKMC_CLOCK_FP64 = 0, FSKMC_CLOCK_FP32 = 1 } fskmc_clock;
    CUDA graph. */
 typedef enum { FSKMC_ENGINE_PLAIN = 0, FSKMC_ENGINE_PERSISTENT = 1 } fskmc_engine;
 
+/* Largest lattice side (and ring length) any entry point accepts; lx*ly is
+   further limited to 2^31 sites. Site coordinates plus a correlation
+   distance then stay within 32-bit integers in every kernel. */
+#define FSKMC_MAX_SIDE (1 << 30)
+
 typedef struct {
     int32_t lx, ly;    /* lattice sides; lx % (2 qx) == 0 and ly % (2 qy) == 0
-                          (ISING1D: ly == 1, a ring of lx sites) */
+                          (ISING1D: ly == 1, a ring of lx sites); each side at most
+                          FSKMC_MAX_SIDE, lx*ly at most 2^31 */
     int32_t bitpacked; /* 1: keep the lattice in device memory at 1 bit per site (32 sites of a
                           row per 32-bit word); spin-flip models only, lx % 32 == 0. The ABI
                           still exchanges one byte per site. Results are identical. */
@@ -383,13 +389,20 @@ fskmc_status fskmc_autotune(int32_t n, const fskmc_lattice *lattices, fskmc_mode
  * library keeps until the process exits; each call clears the part it
  * uses. All calls share that array, so calls that overlap on the GPU (other
  * streams, other host threads) race and give wrong sums: serialise them.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. The call allocates neither device nor host heap memory.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing once the library's device
+ * code is loaded), so a device reset or a new primary context is safe.
+ *
+ * Warm-up: under CUDA's lazy module loading (the default) the first call on
+ * a device loads the library's device code, and loading it does allocate
+ * device memory. Make one call per device at start-up -- before memory runs
+ * short and before any stream capture; later calls allocate neither device
+ * nor host heap memory.
  *
  * EINVAL: NULL lattice/coverage/energy (or paircorr with rmax > 0), unknown
- * model, lx or ly < 1, lx*ly > 2^31, rmax < 0, rmax > lx, rmax > ly when
- * ly > 1, or rmax > FSKMC_NOALLOC_MAX_RMAX. ECUDA: a CUDA call failed.
+ * model, lx or ly < 1 or > FSKMC_MAX_SIDE, lx*ly > 2^31, rmax < 0,
+ * rmax > lx, rmax > ly when ly > 1, or rmax > FSKMC_NOALLOC_MAX_RMAX.
+ * ECUDA: a CUDA call failed.
  */
 #define FSKMC_NOALLOC_MAX_RMAX 256
 fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_t lx, int32_t ly,

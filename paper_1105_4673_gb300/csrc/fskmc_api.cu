@@ -158,6 +158,8 @@ fskmc_status check_geometry(int model, const fskmc_lattice &L, int qx, int qy)
         return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices are for the spin-flip models");
     if (L.bitpacked && L.lx % 32)
         return fail(nullptr, FSKMC_EINVAL, "bit-packed lattices need lx to be a multiple of 32");
+    if (L.lx > FSKMC_MAX_SIDE || L.ly > FSKMC_MAX_SIDE)
+        return fail(nullptr, FSKMC_EINVAL, "lattice side above %d (%d x %d)", FSKMC_MAX_SIDE, L.lx, L.ly);
     if (model == fskmc::ISING1D) {
         // a ring of lx sites: one row of cells qx x 1
         if (L.ly != 1 || qy != 1)

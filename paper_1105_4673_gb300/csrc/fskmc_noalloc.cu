@@ -8,13 +8,13 @@
 // reads the state after an out-of-memory error has no memory left to get.
 // This entry point serves them: its integer accumulators live in a fixed,
 // file-scope device array that every GPU loading the library holds until
-// the process exits, and the call allocates neither device nor host heap
-// memory.
+// the process exits. Once the library's device code is loaded on a device
+// (the first call there, under lazy module loading) a call allocates
+// neither device nor host heap memory.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 
 #include "fskmc.h"
 #include "fskmc_internal.h"
@@ -26,28 +26,14 @@ namespace {
 constexpr int kMaxSlots = 4 + 2 * FSKMC_NOALLOC_MAX_RMAX;
 static __device__ __align__(256) unsigned long long g_obs_scratch[kMaxSlots];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device. Looked up once
-// per device (with that device current) and cached; the host-side symbol
-// itself is not a device address and is never handed to a kernel.
+// Device address of the scratch array on the current device. Looked up on
+// every call (cheap once the module is loaded, and no allocation), so a
+// device reset or a re-created primary context never leaves a stale
+// address; the host-side symbol itself is not a device address and is never
+// handed to a kernel.
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_obs_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
-    return cudaSuccess;
+    return cudaGetSymbolAddress(out, g_obs_scratch);
 }
 
 }  // namespace
@@ -59,7 +45,9 @@ extern "C" fskmc_status fskmc_observables_noalloc(const uint8_t *lattice, int32_
 {
     if (!lattice || !coverage || !energy) return FSKMC_EINVAL;
     if ((int)model < 0 || (int)model > 4) return FSKMC_EINVAL;
-    if (lx < 1 || ly < 1 || (int64_t)lx * ly > ((int64_t)1 << 31)) return FSKMC_EINVAL;
+    if (lx < 1 || ly < 1 || lx > FSKMC_MAX_SIDE || ly > FSKMC_MAX_SIDE ||
+        (int64_t)lx * ly > ((int64_t)1 << 31))
+        return FSKMC_EINVAL;
     if (rmax < 0 || rmax > FSKMC_NOALLOC_MAX_RMAX || rmax > lx || (ly > 1 && rmax > ly))
         return FSKMC_EINVAL;
     if (rmax > 0 && !paircorr) return FSKMC_EINVAL;

@@ -100,3 +100,23 @@ def test_bitpacked_validation(lib, lx, ly, model, q):
     st = lib.fskmc_create(C.byref(F.Lattice(lx, ly, 1)), model, C.byref(F._rates({})),
                           F.CellShape(*q), None, C.byref(h))
     assert st == F.EINVAL and not h.value
+
+
+def test_sides_above_the_limit_are_refused(lib):
+    """Lattice sides above FSKMC_MAX_SIDE (2^30) are refused before any
+    device work, for rings too (a ring of 2^31 - 2 sites would take the
+    observables' site arithmetic past 32 bits), by the context constructor
+    and by the allocation-free observables."""
+    big = 2 ** 31 - 2
+    with pytest.raises(F.FskmcError) as e:
+        F.Context(big, 1, "ISING1D", dict(ka=1.0, kd=1.0, betaJ=1.0), (1, 1))
+    assert e.value.status == F.EINVAL and "side" in str(e.value)
+    with pytest.raises(F.FskmcError) as e:
+        F.Context(2 ** 30 + 2, 2, "ADSDES", dict(ka=1.0, kd=1.0, betaJ=1.0), (1, 1))
+    assert e.value.status == F.EINVAL
+    cov = (C.c_double * 3)()
+    en = C.c_double()
+    for lx, ly in ((big, 1), (2 ** 30 + 2, 1), (1, 2 ** 30 + 2)):
+        st = lib.fskmc_observables_noalloc(16, lx, ly, F.MODELS["ISING1D"], None, cov, C.byref(en),
+                                           None, 0)
+        assert st == F.EINVAL, (lx, ly)

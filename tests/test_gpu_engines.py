@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import paper_1105_4673_gb300 as F
-from gpu_util import gpu_ctx
+from gpu_util import gpu_ctx, match_oracle
 from oracle import closed_forms as CF
 from workloads import random_lattice
 
@@ -43,10 +43,10 @@ def test_persistent_fp64_matches_oracle(model, scheme):
         c.run(scheme, dt, 1.0, 99)
         st = c.stats()
         assert st["check_failures"] == 0 and st["timeouts"] == 0
-        if orc.ambiguous == 0:
-            assert np.array_equal(c.get_state(), orc.lat)
-            assert st["events"] == orc.events
-            assert np.array_equal(c.workload(), orc.workload)
+        got = (c.get_state(), st["events"], c.workload())
+    match_oracle(got, orc, lambda: gpu_ctx(lx, ly, q, model, RATES[model], init, engine="PERSISTENT"),
+                 lambda: oracle.FSRun(lx, ly, *q, model, RATES[model], init), scheme, dt, 1.0, 99,
+                 what=f"persistent {model} {scheme}")
 
 
 def _batch():
@@ -72,11 +72,13 @@ def test_batch_replicas_match_single_contexts(scheme):
             orc.run(scheme, 0.1, 2.0, seed)
             with gpu_ctx(rp["lx"], rp["ly"], (8, 8), "ADSDES", rp["rates"], init, replica=r) as s:
                 s.run(scheme, 0.1, 2.0, seed)
-                alone = s.get_state()
+                alone = (s.get_state(), s.stats()["events"], s.workload())
             got = b.get_state(r)
-            assert np.array_equal(got, alone), f"replica {r}: batch differs from single context"
-            if orc.ambiguous == 0:
-                assert np.array_equal(got, orc.lat), f"replica {r}: differs from the oracle"
+            assert np.array_equal(got, alone[0]), f"replica {r}: batch differs from single context"
+            match_oracle(alone, orc,
+                         lambda: gpu_ctx(rp["lx"], rp["ly"], (8, 8), "ADSDES", rp["rates"], init, replica=r),
+                         lambda: oracle.FSRun(rp["lx"], rp["ly"], 8, 8, "ADSDES", rp["rates"], init, replica=r),
+                         scheme, 0.1, 2.0, seed, replica=r, what=f"replica {r}")
 
 
 @pytest.mark.parametrize("model", list(RATES))

@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import paper_1105_4673_gb300 as F
+from gpu_util import gpu_ctx, match_oracle
 from workloads import WORKLOADS, ensemble_replicas, random_lattice
 
 pytestmark = pytest.mark.gpu
@@ -31,20 +32,27 @@ def _sample_cells(ncx, ncy, colour, n, seed):
     return cells
 
 
-@pytest.mark.parametrize("name,nstates,p,colour,engine", [
-    ("ising1024", 2, None, 0, "PLAIN"),
-    ("ising1024", 2, None, 1, "PERSISTENT"),
-    ("diffusion4096", 2, [0.7, 0.3], 1, "PLAIN"),
-    ("zgb16384", 3, [0.8, 0.1, 0.1], 0, "PLAIN"),
+@pytest.mark.parametrize("name,nstates,p,colour,engine,packed,clock", [
+    ("ising1024", 2, None, 0, "PLAIN", False, "FP64"),
+    ("ising1024", 2, None, 1, "PERSISTENT", False, "FP64"),
+    # the benchmark's own storage and kernel: bit-packed, 4 cells per warp
+    ("ising1024", 2, None, 0, "PLAIN", True, "FP64"),
+    ("ising1024", 2, None, 1, "PERSISTENT", True, "FP64"),
+    ("diffusion4096", 2, [0.7, 0.3], 1, "PLAIN", False, "FP64"),
+    ("zgb16384", 3, [0.8, 0.1, 0.1], 0, "PLAIN", False, "FP64"),
+    ("zgb16384", 3, [0.8, 0.1, 0.1], 1, "PERSISTENT", False, "FP64"),
 ])
-def test_fullsize_window_sampled(name, nstates, p, colour, engine):
+def test_fullsize_window_sampled(name, nstates, p, colour, engine, packed, clock):
     w = WORKLOADS[name]
     lx, ly, (qx, qy) = w["lx"], w["ly"], w["q"]
     lat = random_lattice(lx, ly, nstates, w["seed"], p=p)
     h = w["dt"] if w["scheme"] != "STRANG" else w["dt"] / 2
     widx = 12345
     seed = w["seed"]
-    with F.Context(lx, ly, w["model"], w["rates"], w["q"]) as c:
+    with F.Context(lx, ly, w["model"], w["rates"], w["q"], bitpacked=packed) as c:
+        c.set_clock(clock)
+        if packed:
+            assert c.info()["lanes_per_cell"] == 8  # the grouped kernel the benchmark launches
         c.set_state(lat)
         c.window_index = widx
         if engine == "PLAIN":
@@ -59,12 +67,17 @@ def test_fullsize_window_sampled(name, nstates, p, colour, engine):
     cells = _sample_cells(ncx, ncy, colour, 24, 7)
     ref, ev, amb = oracle.window_cells(lx, ly, qx, qy, w["model"], w["rates"], lat, colour, h,
                                        widx, seed, cells)
+    compared = 0
     for m, e, a in zip(cells, ev, amb):
         ws = oracle.cell_writeset(lx, ly, qx, qy, w["model"], m, colour)
-        if a:
+        if a:  # a flagged cell-window may legitimately differ by one event
             continue
         assert np.array_equal(got[ws], ref[ws]), f"cell {m}"
         assert wl[m] == e, f"cell {m} events"
+        compared += 1
+    # flags are rarer than 1e-6 of the cell-windows: a sample with more than
+    # one is itself a failure, and every test compares at least 23 cells
+    assert int(np.count_nonzero(amb)) <= 1 and compared >= 23, (compared, int(np.count_nonzero(amb)))
 
 
 def test_fullsize_ensemble_sampled_replicas():
@@ -79,10 +92,18 @@ def test_fullsize_ensemble_sampled_replicas():
         b.run(w["scheme"], w["dt"], 0.4, seed)
         assert b.stats()["check_failures"] == 0
         picks = [r for r in range(len(reps)) if reps[r]["lx"] <= 128][:6]
+        wl_all = b.workload
         for r in picks:
             rp = reps[r]
             init = oracle.init_bernoulli(rp["lx"], rp["ly"], seed, w["coverage"], replica=r)
             orc = oracle.FSRun(rp["lx"], rp["ly"], 16, 16, w["model"], rp["rates"], init, replica=r)
             orc.run(w["scheme"], w["dt"], 0.4, seed)
-            if orc.ambiguous == 0:
-                assert np.array_equal(b.get_state(r), orc.lat), f"replica {r}"
+            wl = wl_all(r)
+            # a batch counts events over all replicas: compare the replica's
+            # lattice and its cells' workloads
+            match_oracle((b.get_state(r), None, wl), orc,
+                         lambda: gpu_ctx(rp["lx"], rp["ly"], (16, 16), w["model"], rp["rates"], init,
+                                         engine="PERSISTENT", replica=r),
+                         lambda: oracle.FSRun(rp["lx"], rp["ly"], 16, 16, w["model"], rp["rates"], init,
+                                              replica=r),
+                         w["scheme"], w["dt"], 0.4, seed, replica=r, what=f"replica {r}")

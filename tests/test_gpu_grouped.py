@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import paper_1105_4673_gb300 as F
-from gpu_util import gpu_ctx
+from gpu_util import gpu_ctx, match_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -64,10 +64,10 @@ def test_grouped_matches_oracle_fp64(model, lx, ly, q, lanes, engine):
     assert info["lanes_per_cell"] == lanes
     assert st["check_failures"] == 0 and st["timeouts"] == 0
     assert st["events"] > 0
-    if orc.ambiguous == 0:
-        assert np.array_equal(lat, orc.lat)
-        assert st["events"] == orc.events
-        assert np.array_equal(wl, orc.workload)
+    match_oracle((lat, st["events"], wl), orc,
+                 lambda: gpu_ctx(lx, ly, q, model, RATES[model], init, engine=engine, grouped=True),
+                 lambda: oracle.FSRun(lx, ly, *q, model, RATES[model], init), "LIE", dt, T, seed,
+                 what=f"grouped {model} {lx}x{ly} q={q} {engine}")
 
 
 @pytest.mark.parametrize("model,lx,ly,q,lanes", GEOMS)
@@ -97,8 +97,11 @@ def test_grouped_packed_storage(clock, engine):
         assert np.array_equal(a[0], b[0]) and a[1]["events"] == b[1]["events"]
         if clock == "FP64":
             orc = oracle.FSRun(lx, ly, *q, "ISING", RATES["ISING"], init).run("STRANG", 0.5, 3.0, seed)
-            if orc.ambiguous == 0:
-                assert np.array_equal(a[0], orc.lat) and a[1]["events"] == orc.events
+            match_oracle((a[0], a[1]["events"], a[2]), orc,
+                         lambda: gpu_ctx(lx, ly, q, "ISING", RATES["ISING"], init, engine=engine,
+                                         grouped=True, packed=True),
+                         lambda: oracle.FSRun(lx, ly, *q, "ISING", RATES["ISING"], init),
+                         "STRANG", 0.5, 3.0, seed, what=f"packed {lx}x{ly} q={q} {engine}")
 
 
 @pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
@@ -122,8 +125,9 @@ def test_grouped_uneven_cells_in_a_warp(engine):
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
     orc = oracle.FSRun(lx, ly, *q, "ADSDES", rates, init).run("LIE", 0.5, 4.0, 17)
-    if orc.ambiguous == 0:
-        assert np.array_equal(out[0][0], orc.lat) and out[0][1] == orc.events
+    match_oracle(out[0], orc, lambda: gpu_ctx(lx, ly, q, "ADSDES", rates, init, engine=engine, grouped=True),
+                 lambda: oracle.FSRun(lx, ly, *q, "ADSDES", rates, init), "LIE", 0.5, 4.0, 17,
+                 what=f"bump start {engine}")
 
 
 @pytest.mark.parametrize("clock", ["FP64", "FP32"])
@@ -246,8 +250,9 @@ def test_dyadic_and_zero_rates_match_oracle(model, rates, engine):
             c.set_cell_grouping(grouped)
             c.set_state(init)
             c.run("STRANG", 0.5, 3.0, seed)
-            res.append((c.get_state(), c.stats()["events"]))
+            res.append((c.get_state(), c.stats()["events"], c.workload()))
     assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] > 0
     orc = oracle.FSRun(lx, ly, *q, model, rates, init).run("STRANG", 0.5, 3.0, seed)
-    if orc.ambiguous == 0:
-        assert np.array_equal(res[0][0], orc.lat) and res[0][1] == orc.events
+    match_oracle(res[0], orc, lambda: gpu_ctx(lx, ly, q, model, rates, init, engine=engine, grouped=True),
+                 lambda: oracle.FSRun(lx, ly, *q, model, rates, init), "STRANG", 0.5, 3.0, seed,
+                 what=f"{model} {rates} {engine}")

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import paper_1105_4673_gb300 as F
-from gpu_util import gpu_ctx, windowwise
+from gpu_util import gpu_ctx, match_oracle
 from oracle import closed_forms as CF
 
 pytestmark = pytest.mark.gpu
@@ -42,15 +42,10 @@ def _bit_exact(L, q, rates, scheme, dt, T, seed, engine="PLAIN", bitpacked=False
         c.set_state(init)
         c.run(scheme, dt, T, seed)
         g, st, wl = c.get_state(), c.stats(), c.workload()
-    if orc.ambiguous == 0:
-        assert np.array_equal(g, orc.lat)
-        assert st["events"] == orc.events
-        assert np.array_equal(wl, orc.workload)
-    else:
-        col, h = oracle.schedule(scheme, dt, T, seed)
-        orc2 = oracle.FSRun(L, 1, q, 1, "ISING1D", rates, init)
-        with gpu_ctx(L, 1, (q, 1), "ISING1D", rates, init) as c2:
-            windowwise(c2, orc2, col, h, seed)
+    match_oracle((g, st["events"], wl), orc,
+                 lambda: gpu_ctx(L, 1, (q, 1), "ISING1D", rates, init, engine=engine, packed=bitpacked),
+                 lambda: oracle.FSRun(L, 1, q, 1, "ISING1D", rates, init), scheme, dt, T, seed,
+                 what=f"ring {L} q={q} {scheme} {engine}")
     assert st["events"] > 0
 
 
@@ -85,9 +80,11 @@ def test_ring_full_size_bit_exact():
         c.set_engine("PERSISTENT")
         c.set_state(init)
         c.run("LIE", 1.0, 8.0, 99)
-        g, ev = c.get_state(), c.stats()["events"]
+        got = (c.get_state(), c.stats()["events"], c.workload())
     orc = oracle.FSRun(L, 1, qx, 1, "ISING1D", rates, init).run("LIE", 1.0, 8.0, 99)
-    assert orc.ambiguous > 0 or (np.array_equal(g, orc.lat) and ev == orc.events)
+    match_oracle(got, orc, lambda: gpu_ctx(L, 1, (qx, 1), "ISING1D", rates, init, engine="PERSISTENT"),
+                 lambda: oracle.FSRun(L, 1, qx, 1, "ISING1D", rates, init), "LIE", 1.0, 8.0, 99,
+                 what="2^15 ring")
 
 
 def test_ring_observables_bit_exact():

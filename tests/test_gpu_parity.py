@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import paper_1105_4673_gb300 as F
-from gpu_util import gpu_ctx, windowwise
+from gpu_util import gpu_ctx, match_oracle
 from workloads import WORKLOADS, random_lattice
 
 pytestmark = pytest.mark.gpu
@@ -65,15 +65,10 @@ def test_run_bit_exact(model, lx, ly, q, scheme):
         g = c.get_state()
         st = c.stats()
         wl = c.workload()
-    if orc.ambiguous == 0:
-        assert np.array_equal(g, orc.lat)
-        assert st["events"] == orc.events
-        assert np.array_equal(wl, orc.workload)
-    else:  # redo window by window with resync at flagged windows
-        col, h = oracle.schedule(scheme, dt, T, seed)
-        orc2 = oracle.FSRun(lx, ly, *q, model, RATES[model], init)
-        with gpu_ctx(lx, ly, q, model, RATES[model], init) as c2:
-            windowwise(c2, orc2, col, h, seed)
+    match_oracle((g, st["events"], wl), orc,
+                 lambda: gpu_ctx(lx, ly, q, model, RATES[model], init),
+                 lambda: oracle.FSRun(lx, ly, *q, model, RATES[model], init),
+                 scheme, dt, T, seed, what=f"{model} {lx}x{ly} q={q} {scheme}")
     assert st["windows"] == orc.windows and st["events"] > 0
 
 
@@ -126,7 +121,10 @@ def test_launch_shape_invariance(wpb):
     orc = oracle.FSRun(lx, ly, *q, model, RATES[model], init).run("STRANG", 0.1, 1.0, 4)
     with gpu_ctx(lx, ly, q, model, RATES[model], init, wpb=wpb) as c:
         c.run("STRANG", 0.1, 1.0, 4)
-        assert np.array_equal(c.get_state(), orc.lat)
+        got = (c.get_state(), c.stats()["events"], c.workload())
+    match_oracle(got, orc, lambda: gpu_ctx(lx, ly, q, model, RATES[model], init, wpb=wpb),
+                 lambda: oracle.FSRun(lx, ly, *q, model, RATES[model], init), "STRANG", 0.1, 1.0, 4,
+                 what=f"{wpb} warps per block")
 
 
 @pytest.mark.parametrize("model", ["ADSDES", "DIFFUSION", "ZGB"])
@@ -154,3 +152,28 @@ def test_invalid_state_rejected():
         assert e.value.status == F.EINVAL
         with pytest.raises(F.FskmcError):
             c.run("LIE", 0.3, 1.0, 1)  # T/dt not an integer
+
+
+def test_flagged_window_takes_the_replay_path():
+    """A window whose length equals cell 0's first waiting time puts that
+    edge decision exactly on the window end: the oracle flags the
+    cell-window, and the comparison replays the run window by window
+    (resyncing at most at the flagged window) instead of skipping it."""
+    import math
+    lx, ly, q = 16, 16, (4, 4)
+    rates = dict(ka=1.0, kd=1.0, betaJ=0.0)  # every site rate 1: lambda = 16 in every cell
+    seed = 0x5151
+    o = oracle.philox([0, 0, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])  # (e, w, m, replica|tag 0)
+    u = ((int(o[0]) << 21 | int(o[1]) >> 11) + 1) * 2.0 ** -53
+    h = -math.log(u) / 16.0
+    init = oracle.init_bernoulli(lx, ly, seed, 0.5)
+    orc = oracle.FSRun(lx, ly, *q, "ADSDES", rates, init).run("LIE", h, h, seed)
+    assert orc.ambiguous >= 1
+    for engine in ("PLAIN", "PERSISTENT"):
+        with gpu_ctx(lx, ly, q, "ADSDES", rates, init, engine=engine) as c:
+            c.run("LIE", h, h, seed)
+            got = (c.get_state(), c.stats()["events"], c.workload())
+        n = match_oracle(got, orc, lambda: gpu_ctx(lx, ly, q, "ADSDES", rates, init, engine=engine),
+                         lambda: oracle.FSRun(lx, ly, *q, "ADSDES", rates, init), "LIE", h, h, seed,
+                         what=f"flagged window, {engine}")
+        assert n <= 1

@@ -3,15 +3,18 @@
 Some callers cannot let a library allocate device memory (their memory
 belongs to their own pool, or they read the state after running out of
 memory). This entry point keeps its accumulators in a fixed device array
-inside the library. Here it must give exactly what fskmc_observables gives
-(the sums are exact integers, so the results are bit-identical), on two
-calls in a row, since the array keeps the previous call's contents.
+inside the library. Here it must give exactly the oracle's observables (the
+sums are exact integers, so the results are bit-identical) and what
+fskmc_observables gives, on two calls in a row, since the array keeps the
+previous call's contents; and, after one warm-up call has loaded the
+library's device code, a call must leave the device's free memory unchanged.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_1105_4673_gb300 as F
 from workloads import random_lattice
 
@@ -24,6 +27,12 @@ def _lib():
     build.build()
     import torch
     assert torch.cuda.is_available()
+    # the warm-up call the header asks for: under lazy module loading the
+    # first call on a device loads the library's device code
+    dev = torch.zeros(64 * 64, dtype=torch.uint8, device="cuda")
+    st, *_ = _noalloc(dev.data_ptr(), 64, 64, "ISING", 1, None)
+    torch.cuda.synchronize()
+    assert st == F.OK
 
 
 def _noalloc(ptr, lx, ly, model, rmax, stream):
@@ -34,6 +43,12 @@ def _noalloc(ptr, lx, ly, model, rmax, stream):
     st = L.fskmc_observables_noalloc(ptr, lx, ly, F.MODELS[model], stream, cov, C.byref(en), pc,
                                      rmax)
     return st, np.array(cov[:]), en.value, np.array(pc[:2 * rmax])
+
+
+def _same(got, want):
+    cov, en, pc = got
+    return (np.array_equal(cov, want[0]) and ((np.isnan(en) and np.isnan(want[1])) or en == want[1])
+            and np.array_equal(pc, want[2]))
 
 
 @pytest.mark.parametrize("model,lx,ly,rmax1,rmax2", [("ISING", 128, 96, 32, 8),
@@ -51,11 +66,28 @@ def test_noalloc_matches_observables_twice(model, lx, ly, rmax1, rmax2):
             dev = torch.empty(lx * ly, dtype=torch.uint8, device="cuda")
             c.get_state(0, out=dev)
             c.sync()
-            st, cov, en, pc = _noalloc(dev.data_ptr(), lx, ly, model, rmax, stream.cuda_stream)
+            st, *got = _noalloc(dev.data_ptr(), lx, ly, model, rmax, stream.cuda_stream)
             assert st == F.OK, f"call {call}"
-            assert np.array_equal(cov, want[0]), f"call {call}"
-            assert (np.isnan(en) and np.isnan(want[1])) or en == want[1], f"call {call}"
-            assert np.array_equal(pc, want[2]), f"call {call}"
+            assert _same(got, want), f"call {call}: differs from fskmc_observables"
+            assert _same(got, oracle.observables(lx, ly, model, lat, rmax)), f"call {call}: differs from the oracle"
+
+
+def test_noalloc_allocates_nothing():
+    """A call on a 2048 x 1024 lattice at the largest rmax leaves the
+    device's free memory unchanged, and still equals the oracle."""
+    import torch
+    lx, ly = 2048, 1024
+    lat = random_lattice(lx, ly, 3, 9, p=[0.5, 0.3, 0.2])
+    dev = torch.from_numpy(lat).to("cuda")
+    rmax = F.NOALLOC_MAX_RMAX
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    st, *got = _noalloc(dev.data_ptr(), lx, ly, "ZGB", rmax, None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert st == F.OK
+    assert free1 == free0, (free0, free1)
+    assert _same(got, oracle.observables(lx, ly, "ZGB", lat, rmax))
 
 
 def test_noalloc_rejects_sizes_beyond_the_limit():
