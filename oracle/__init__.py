@@ -42,8 +42,8 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-pthread", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -99,6 +99,18 @@ def lib():
                                                        C.c_uint64, C.c_uint32, u8p, C.c_int, i32p,
                                                        i32p, i32p]
         L.orc_window_cells.restype = C.c_int
+        L.orc_fs_run_threads.argtypes = [C.c_int] * 5 + [f64p, C.c_int, C.c_double, C.c_double,
+                                                         C.c_uint64, C.c_uint32, u32p, u8p, u64p,
+                                                         C.c_void_p, C.c_int]
+        L.orc_fs_run_threads.restype = C.c_int
+        L.orc_fs2_run.argtypes = [C.c_int] * 7 + [f64p, C.c_int, C.c_double, C.c_double, C.c_int,
+                                                  C.c_int, C.c_uint64, C.c_uint32, u32p, u8p, u64p,
+                                                  C.c_void_p]
+        L.orc_fs2_run.restype = C.c_int
+        L.orc_fs2_ensemble.argtypes = [C.c_int] * 7 + [f64p, C.c_int, C.c_double, C.c_double,
+                                                       C.c_int, C.c_int, C.c_uint64, C.c_int, u8p,
+                                                       u8p]
+        L.orc_fs2_ensemble.restype = C.c_int
         _lib = L
     return _lib
 
@@ -180,6 +192,16 @@ class FSRun:
             raise ValueError("oracle rejected the run arguments")
         return self
 
+    def run_threads(self, scheme, dt, T, seed, nthreads: int):
+        """The same run with each window's cells spread over nthreads threads
+        (bit-identical to run(): same-colour cells are independent)."""
+        rc = lib().orc_fs_run_threads(self.lx, self.ly, self.qx, self.qy, self.model, self.r6,
+                                      _scheme(scheme), dt, T, seed, self.replica, self.w, self.lat,
+                                      self.stats, self.workload.ctypes.data, nthreads)
+        if rc != 0:
+            raise ValueError("oracle rejected the run arguments")
+        return self
+
     def window(self, colour: int, h: float, seed: int, w: int | None = None):
         """One window; returns per-cell ambiguous flags."""
         amb = np.zeros_like(self.workload)
@@ -203,6 +225,61 @@ class FSRun:
     @property
     def ambiguous(self) -> int:
         return int(self.stats[2])
+
+
+class FS2Run:
+    """Nested (two-level) FS run on one lattice, Section 5 (Eq. sublatt2,
+    Eq. opdecomp2): super-cells Qx x Qy in a checkerboard, each a
+    checkerboard of sub-cells qx x qy; the outer schedule over super-cell
+    colours, n_in inner steps of the inner schedule (LIE or STRANG) over the
+    sub-cell colours inside every outer window. Spin-flip models only."""
+
+    def __init__(self, lx, ly, Q, q, model, rates: dict, lattice=None, replica: int = 0):
+        self.lx, self.ly = lx, ly
+        self.Qx, self.Qy = Q
+        self.qx, self.qy = q
+        self.model = _model(model)
+        self.r6 = _rates6(rates)
+        self.replica = replica
+        self.lat = (np.zeros(lx * ly, np.uint8) if lattice is None
+                    else np.ascontiguousarray(lattice, dtype=np.uint8).reshape(-1).copy())
+        self.w = np.zeros(1, np.uint32)
+        self.stats = np.zeros(3, np.uint64)
+        self.workload = np.zeros((lx // self.qx) * (ly // self.qy), np.int32)
+
+    def run(self, scheme, dt, T, seed, inner="LIE", n_in: int = 1):
+        rc = lib().orc_fs2_run(self.lx, self.ly, self.Qx, self.Qy, self.qx, self.qy, self.model,
+                               self.r6, _scheme(scheme), dt, T, _scheme(inner), n_in, seed,
+                               self.replica, self.w, self.lat, self.stats,
+                               self.workload.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle rejected the nested run arguments")
+        return self
+
+    @property
+    def events(self) -> int:
+        return int(self.stats[0])
+
+    @property
+    def windows(self) -> int:
+        return int(self.stats[1])
+
+    @property
+    def ambiguous(self) -> int:
+        return int(self.stats[2])
+
+
+def fs2_ensemble(lx, ly, Q, q, model, rates: dict, scheme, dt, T, seed, M, init, inner="LIE",
+                 n_in: int = 1) -> np.ndarray:
+    """Final states (M, lx*ly) of M independent nested runs (replicas 0..M-1)."""
+    init = np.ascontiguousarray(init, dtype=np.uint8).reshape(-1)
+    out = np.zeros((M, lx * ly), np.uint8)
+    rc = lib().orc_fs2_ensemble(lx, ly, Q[0], Q[1], q[0], q[1], _model(model), _rates6(rates),
+                                _scheme(scheme), dt, T, _scheme(inner), n_in, seed, M, init,
+                                out.reshape(-1))
+    if rc != 0:
+        raise ValueError("oracle rejected the ensemble arguments")
+    return out
 
 
 def ssa_run(lx, ly, model, rates: dict, lattice, T: float, seed: int, replica: int = 0):

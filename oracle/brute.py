@@ -284,3 +284,64 @@ def window_frozen_halo(lx, ly, qx, qy, model, rates, snapshot, colour, h, cell):
     p0 = np.zeros(n)
     p0[int(snap[ws].astype(np.int64) @ pw)] = 1.0
     return ws, evolve(p0, Q.tocsr(), h)
+
+
+def nested_colours(lx, ly, Qx, Qy, qx, qy, i):
+    """(super-cell colour, sub-cell colour) of site i in the two-level
+    checkerboard of Eq. sublatt2: super-cells Qx x Qy coloured by
+    (cx + cy) mod 2, and inside each super-cell the sub-cells qx x qy coloured
+    by their position within it."""
+    x, y = i % lx, i // lx
+    C = ((x // Qx) + (y // Qy)) % 2
+    c = (((x % Qx) // qx) + ((y % Qy) // qy)) % 2
+    return C, c
+
+
+def generator_nested(lx, ly, Qx, Qy, qx, qy, model, rates, C, c):
+    """Sparse generator of the site events of one (super colour, sub colour)
+    part of Eq. opdecomp2 (spin-flip models: every event is a site event)."""
+    S, base, evs = events(lx, ly, model, rates)
+    assert model in ("ADSDES", "ISING")
+    nstate = len(S)
+    pw = base ** np.arange(lx * ly, dtype=np.int64)
+    codes = S.astype(np.int64) @ pw
+    rows, cols, vals = [], [], []
+    for owner, sites, newv, cv in evs:
+        if nested_colours(lx, ly, Qx, Qy, qx, qy, owner[1]) != (C, c):
+            continue
+        nz = cv > 0
+        tgt = codes + (newv[0].astype(np.int64) - S[:, sites[0]].astype(np.int64)) * pw[sites[0]]
+        rows.append(codes[nz]); cols.append(tgt[nz]); vals.append(cv[nz])
+    Q = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nstate, nstate)).tocsr()
+    Q = Q - sp.diags(np.asarray(Q.sum(axis=1)).ravel())
+    return Q.tocsr()
+
+
+def nested_window(p, QC, h, inner, n_in):
+    """One outer window of length h of one super-cell colour: n_in inner
+    steps of the inner splitting over its two sub-cell colours QC = (Q_C0,
+    Q_C1) -- Lie: e^{d Q_C0} e^{d Q_C1}; Strang: e^{d/2 Q_C0} e^{d Q_C1}
+    e^{d/2 Q_C0}; d = h / n_in."""
+    d = h / n_in
+    for _ in range(n_in):
+        if inner == "LIE":
+            p = evolve(evolve(p, QC[0], d), QC[1], d)
+        else:
+            p = evolve(evolve(evolve(p, QC[0], d / 2), QC[1], d), QC[0], d / 2)
+    return p
+
+
+def nested_product(p, Qs, scheme, dt, n, inner, n_in):
+    """Law after n outer steps of the nested scheme (Eq. opdecomp2 composed
+    by Eq. lie or Eq. strang at both levels). Qs[C][c] is the generator of
+    super colour C, sub colour c."""
+    for _ in range(n):
+        if scheme == "LIE":
+            p = nested_window(p, Qs[0], dt, inner, n_in)
+            p = nested_window(p, Qs[1], dt, inner, n_in)
+        else:
+            p = nested_window(p, Qs[0], dt / 2, inner, n_in)
+            p = nested_window(p, Qs[1], dt, inner, n_in)
+            p = nested_window(p, Qs[0], dt / 2, inner, n_in)
+    return p

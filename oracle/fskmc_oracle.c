@@ -23,6 +23,11 @@
  *                    lattices (chi-square); the J=0 closed form; Onsager
  *   orc_ssa_run      exact e^{TQ} on 3x3 (chi-square); the J=0 closed form
  *   orc_observables  brute-force recount in numpy
+ *   orc_fs_run_threads  equal, lattice for lattice, to orc_fs_run (the cells
+ *                    of one colour are independent, Eq. exact)
+ *   orc_fs2_run      exact nested operator products (Eq. opdecomp2) on a 4x4
+ *                    lattice (chi-square); the Trotter limit of the inner
+ *                    splitting on the exact products
  *
  * Conventions (the paper is silent on all of these; the readings are the
  * project's contract and are shared, by specification only, with the CUDA
@@ -53,6 +58,7 @@
  *             window edge is discarded.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -843,6 +849,225 @@ int orc_fs_ensemble(int lx, int ly, int qx, int qy, int model,
         memcpy(lat, init, N);
         if (orc_fs_run(lx, ly, qx, qy, model, rates7, scheme, dt, T, seed,
                        (uint32_t)r, &w, 0, lat, st, NULL))
+            return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same FS run with the cells of each window spread over threads.       */
+/* Same-colour cells read only the window-start snapshot outside their own  */
+/* write sets and write disjoint write sets (Eq. exact), so the result does */
+/* not depend on which thread runs which cell: it equals orc_fs_run's, bit  */
+/* for bit. Each thread keeps its own private copy, stamps and member list; */
+/* the snapshot is shared. Threads take cells from a shared counter.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const sys_t *S;
+    uint8_t *lat, *snap;
+    const int32_t *col;
+    const double *hh;
+    int64_t nw;
+    uint32_t w0, rep;
+    uint64_t seed;
+    int32_t *workload;
+    int *cells[2];
+    int ncells[2];
+    int next;
+    pthread_barrier_t bar;
+} tshared_t;
+
+typedef struct {
+    tshared_t *sh;
+    work_t W;
+    int tid;
+    uint64_t ev, amb;
+} tworker_t;
+
+static void *thread_windows(void *arg)
+{
+    tworker_t *T = (tworker_t *)arg;
+    tshared_t *sh = T->sh;
+    const sys_t *S = sh->S;
+    size_t N = (size_t)S->lx * S->ly;
+    for (int64_t i = 0; i < sh->nw; i++) {
+        const int c = sh->col[i];
+        if (T->tid == 0) {
+            memcpy(sh->snap, sh->lat, N);
+            __atomic_store_n(&sh->next, 0, __ATOMIC_SEQ_CST);
+        }
+        pthread_barrier_wait(&sh->bar);
+        for (;;) {
+            int j = __atomic_fetch_add(&sh->next, 1, __ATOMIC_SEQ_CST);
+            if (j >= sh->ncells[c]) break;
+            int m = sh->cells[c][j];
+            int a = 0;
+            uint32_t e = cell_window(&T->W, sh->lat, m % S->ncx, m / S->ncx, c, sh->hh[i],
+                                     sh->w0 + (uint32_t)i, sh->rep, sh->seed, &a);
+            T->ev += e;
+            T->amb += (uint64_t)a;
+            if (sh->workload) sh->workload[m] = (int32_t)e;
+        }
+        pthread_barrier_wait(&sh->bar);
+    }
+    return NULL;
+}
+
+int orc_fs_run_threads(int lx, int ly, int qx, int qy, int model, const double *rates7,
+                       int scheme, double dt, double T, uint64_t seed, uint32_t rep,
+                       uint32_t *w, uint8_t *lat, uint64_t *stats_out, int32_t *workload,
+                       int nthreads)
+{
+    sys_t S;
+    if (nthreads < 1 || nthreads > 1024) return -1;
+    if (!geometry_ok(model, lx, ly, qx, qy)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
+    int64_t nw = orc_schedule(scheme, dt, T, seed, rep, *w, NULL, NULL, 0);
+    if (nw < 0) return -1;
+    tshared_t sh;
+    memset(&sh, 0, sizeof sh);
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nw + 1));
+    double *hh = (double *)malloc(sizeof(double) * (size_t)(nw + 1));
+    uint8_t *snap = (uint8_t *)malloc((size_t)lx * ly);
+    int nc = S.ncx * S.ncy;
+    sh.cells[0] = (int *)malloc(sizeof(int) * (size_t)nc);
+    sh.cells[1] = (int *)malloc(sizeof(int) * (size_t)nc);
+    tworker_t *tw = (tworker_t *)calloc((size_t)nthreads, sizeof(tworker_t));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    int rc = -1, inited = 0;
+    if (!col || !hh || !snap || !sh.cells[0] || !sh.cells[1] || !tw || !th) goto done;
+    orc_schedule(scheme, dt, T, seed, rep, *w, col, hh, nw);
+    for (int m = 0; m < nc; m++) {
+        int c = ((m % S.ncx) + (m / S.ncx)) & 1;
+        sh.cells[c][sh.ncells[c]++] = m;
+    }
+    sh.S = &S; sh.lat = lat; sh.snap = snap; sh.col = col; sh.hh = hh; sh.nw = nw;
+    sh.w0 = *w; sh.rep = rep; sh.seed = seed; sh.workload = workload;
+    for (; inited < nthreads; inited++) {
+        tw[inited].sh = &sh;
+        tw[inited].tid = inited;
+        if (work_init(&tw[inited].W, &S)) { work_free(&tw[inited].W); goto done; }
+        free(tw[inited].W.snap);
+        tw[inited].W.snap = snap;   /* the shared window-start snapshot */
+    }
+    pthread_barrier_init(&sh.bar, NULL, (unsigned)nthreads);
+    for (int t = 1; t < nthreads; t++) pthread_create(&th[t], NULL, thread_windows, &tw[t]);
+    thread_windows(&tw[0]);
+    for (int t = 1; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_barrier_destroy(&sh.bar);
+    for (int t = 0; t < nthreads; t++) {
+        stats_out[0] += tw[t].ev;
+        stats_out[2] += tw[t].amb;
+    }
+    stats_out[1] += (uint64_t)nw;
+    *w += (uint32_t)nw;
+    rc = 0;
+done:
+    for (int t = 0; t < inited; t++) {
+        tw[t].W.snap = NULL;
+        work_free(&tw[t].W);
+    }
+    free(col); free(hh); free(snap); free(sh.cells[0]); free(sh.cells[1]); free(tw); free(th);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nested (two-level) decomposition, Section 5 (Eq. sublatt2, Eq. opdecomp2)*/
+/* The lattice is a checkerboard of super-cells Qx*Qy (colours E/O, as in   */
+/* Eq. sublatt); every super-cell is itself a checkerboard of sub-cells     */
+/* qx*qy (Eq. sublatt2), so L^E_m = L^EE_m + L^EO_m. The outer schedule     */
+/* (Lie, Strang, random) runs over the super-cell colours with step dt as   */
+/* in orc_fs_run; within an outer window of colour C and length h every     */
+/* super-cell of colour C runs the inner schedule over its sub-cell colours */
+/* with n_in inner steps of length h/n_in: inner Lie  EE(d) EO(d), inner    */
+/* Strang EE(d/2) EO(d) EE(d/2) per inner step. Every inner window is an FS */
+/* window of the sub-cells of one inner colour inside the super-cells of    */
+/* colour C (the sub-cell checkerboard of a super-cell is the global one    */
+/* since Qx/qx and Qy/qy are even), reading the lattice as it was when the  */
+/* inner window began. Spin-flip models only: there every event is a site   */
+/* event, so both levels of the decomposition are the site partition.       */
+/* Draws: the inner window j of outer window W uses window index            */
+/* W * ninner + j (ninner = 2 n_in for inner Lie, 3 n_in for inner Strang)  */
+/* and the sub-cell's id in the global sub-cell grid.                       */
+/* stats_out = {events, inner windows, ambiguous}; *w counts outer windows. */
+/* ------------------------------------------------------------------------ */
+static int nested_ok(int model, int lx, int ly, int Qx, int Qy, int qx, int qy, int inner, int n_in)
+{
+    if (model != ORC_ADSDES && model != ORC_ISING) return 0;
+    if (inner != ORC_LIE && inner != ORC_STRANG) return 0;
+    if (n_in < 1) return 0;
+    if (qx < 1 || qy < 1 || Qx < 2 * qx || Qy < 2 * qy) return 0;
+    if (Qx % (2 * qx) || Qy % (2 * qy)) return 0;
+    if (lx < 2 * Qx || ly < 2 * Qy || lx % (2 * Qx) || ly % (2 * Qy)) return 0;
+    return geometry_ok(model, lx, ly, qx, qy);
+}
+
+int orc_fs2_run(int lx, int ly, int Qx, int Qy, int qx, int qy, int model,
+                const double *rates7, int scheme, double dt, double T, int inner, int n_in,
+                uint64_t seed, uint32_t rep, uint32_t *w, uint8_t *lat, uint64_t *stats_out,
+                int32_t *workload)
+{
+    sys_t S;
+    if (!nested_ok(model, lx, ly, Qx, Qy, qx, qy, inner, n_in)) return -1;
+    if (sys_init(&S, lx, ly, qx, qy, model, rates7)) return -1;
+    int64_t nw = orc_schedule(scheme, dt, T, seed, rep, *w, NULL, NULL, 0);
+    if (nw < 0) return -1;
+    const int64_t ninner = (inner == ORC_LIE ? 2 : 3) * (int64_t)n_in;
+    if (((int64_t)*w + nw) * ninner > (int64_t)UINT32_MAX) return -1;
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nw + 1));
+    double *hh = (double *)malloc(sizeof(double) * (size_t)(nw + 1));
+    work_t W;
+    memset(&W, 0, sizeof W);
+    if (!col || !hh || work_init(&W, &S)) { work_free(&W); free(col); free(hh); return -1; }
+    orc_schedule(scheme, dt, T, seed, rep, *w, col, hh, nw);
+    const size_t N = (size_t)lx * ly;
+    const int rx = Qx / qx, ry = Qy / qy;   /* sub-cells per super-cell side */
+    uint64_t ev = 0, amb = 0;
+    for (int64_t i = 0; i < nw; i++) {
+        const int C = col[i];
+        const double d = hh[i] / (double)n_in;
+        const uint32_t W0 = (uint32_t)((*w + (uint32_t)i) * ninner);
+        for (int64_t j = 0; j < ninner; j++) {
+            int cin;
+            double len;
+            if (inner == ORC_LIE) { cin = (int)(j % 2); len = d; }
+            else { int p = (int)(j % 3); cin = p == 1; len = p == 1 ? d : d * 0.5; }
+            memcpy(W.snap, lat, N);
+            for (int m = 0; m < S.ncx * S.ncy; m++) {
+                const int sx = m % S.ncx, sy = m / S.ncx;
+                if (((sx + sy) & 1) != cin) continue;
+                if ((((sx / rx) + (sy / ry)) & 1) != C) continue;
+                int a = 0;
+                uint32_t e = cell_window(&W, lat, sx, sy, cin, len, W0 + (uint32_t)j, rep, seed, &a);
+                ev += e;
+                amb += (uint64_t)a;
+                if (workload) workload[m] = (int32_t)e;
+            }
+        }
+    }
+    *w += (uint32_t)nw;
+    stats_out[0] += ev;
+    stats_out[1] += (uint64_t)(nw * ninner);
+    stats_out[2] += amb;
+    work_free(&W);
+    free(col);
+    free(hh);
+    return 0;
+}
+
+/* M independent nested runs (replicas 0..M-1) from the same initial state. */
+int orc_fs2_ensemble(int lx, int ly, int Qx, int Qy, int qx, int qy, int model,
+                     const double *rates7, int scheme, double dt, double T, int inner,
+                     int n_in, uint64_t seed, int M, const uint8_t *init, uint8_t *out)
+{
+    size_t N = (size_t)lx * ly;
+    for (int r = 0; r < M; r++) {
+        uint8_t *lat = out + (size_t)r * N;
+        uint32_t w = 0;
+        uint64_t st[3] = {0, 0, 0};
+        memcpy(lat, init, N);
+        if (orc_fs2_run(lx, ly, Qx, Qy, qx, qy, model, rates7, scheme, dt, T, inner, n_in,
+                        seed, (uint32_t)r, &w, lat, st, NULL))
             return -1;
     }
     return 0;
