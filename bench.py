@@ -1,15 +1,24 @@
 """Benchmark: KMC events/s of the fractional-step sweep on one GB300.
 
-Workload (default): the 2D Ising spin-flip Arrhenius benchmark of Section 7
-on a 1024x1024 periodic lattice at betaJ = 0.4407, 16x16 cells, Lie
-splitting with dt = 1, binary64 window clocks. One step = 10 units of
-physical time (20 fractional windows) plus the observables (coverage,
-energy, pair correlations up to r = 32): every stage of the hot path.
+Workload (default): the ZGB catalytic surface of Section 7.1 on a 16384 x
+16384 periodic lattice (three states, one byte per site, 32 x 32 cells),
+empty with a seeded Gaussian bump of species A, Strang splitting with
+dt = 0.02. One step = 10 dt of physical time (30 fractional windows) through
+fskmc_run, plus the observables (coverage per species, energy, pair
+correlations up to r = 32): every stage of the hot path.
 
-Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on
-a bounded sample of the same workload instead. Under torchrun each rank runs
-its own independent lattice (replicas only: the path needs no collective);
-the barrier and the max-over-ranks timing use torch.distributed.
+The line compares, on the same workload in the same run, the batched
+binary32-clock form (the persistent, graph-launched engine with per-cell
+binary32 clocks over exact integer class sums; `value`) with the plain
+binary64 form (one launch per window, the oracle's arithmetic bit for bit),
+and states the dt-error of each observable (against the same scheme at
+dt/8, the serial-SSA limit up to 1/64 of the error for a second-order
+splitting) with its standard error over independent runs.
+
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead. Under torchrun each rank runs its own independent lattice
+(replicas only: the path needs no collective); the barrier and the
+max-over-ranks timing use torch.distributed.
 """
 from __future__ import annotations
 
@@ -26,12 +35,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import WORKLOADS, sample_shape  # noqa: E402
+from workloads import WORKLOADS, cpu_sample  # noqa: E402
 
 METRIC = "KMC events/sec on 1 GB300 (batched FP32-clock vs plain FP64) at stated Δt-error"
 STEP_WINDOWS_DT = 10  # one bench step advances the lattice by 10 dt of physical time
 RMAX = 32
 L2_FLUSH_BYTES = 256 << 20
+FORMS = {"batched_fp32": ("PERSISTENT", "FP32"), "plain_fp64": ("PLAIN", "FP64"),
+         "plain_fp32": ("PLAIN", "FP32"), "persistent_fp64": ("PERSISTENT", "FP64")}
 
 
 def parse():
@@ -40,11 +51,16 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="ising1024")
+    p.add_argument("--workload", default="zgb16384")
+    p.add_argument("--form", default="batched_fp32", choices=list(FORMS),
+                   help="the form `value` reports (the metric's batched binary32-clock form by default)")
+    p.add_argument("--compare", default="plain_fp64", choices=list(FORMS) + ["none"],
+                   help="the form timed beside it on the same workload")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
-    p.add_argument("--no-variants", action="store_true")
-    p.add_argument("--engine", default="plain", choices=["plain", "persistent"])
-    p.add_argument("--clock", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--no-variants", action="store_true", help="skip the other two forms")
+    p.add_argument("--dt-error-runs", type=int, default=4,
+                   help="independent runs per arm of the dt-error estimate (0: skip)")
+    p.add_argument("--dt-error-T", type=float, default=2.56, help="physical time of the dt-error runs")
     p.add_argument("--wpb", type=int, default=0, help="warps per CTA (0: the library default)")
     p.add_argument("--order", default="auto", choices=["auto", "natural", "workload"],
                    help="issue order of a window's active cells")
@@ -53,6 +69,12 @@ def parse():
     p.add_argument("--grouping", default="auto", choices=["auto", "on", "off"],
                    help="several small spin-flip cells per warp (on), one cell per warp (off), "
                         "or the library's choice (auto)")
+    p.add_argument("--clock", default="fp32", choices=["fp64", "fp32"], help="ensemble512 only")
+    p.add_argument("--study", default=None, choices=["weak-order", "weak-order-replicas", "clock-error"],
+                   help="instead of the throughput line: the weak-order study of the 1024^2 Ising "
+                        "workload (Lie and Strang, dt in {1, 1/2, 1/4, 1/8} against the dt -> 0 "
+                        "limit), or the binary32-vs-binary64 clock error of the workload's observables")
+    p.add_argument("--betaJ", type=float, default=None, help="weak-order study: coupling (default: the workload's)")
     return p.parse_args()
 
 
@@ -118,51 +140,50 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-# Roofline of the window kernels. The per-event arithmetic of the clock
-# contract is K + 4 operations: the ordered fused multiply-add chain over
-# the model's K classes (binary64) or the exact fixed-point class sums
-# (binary32 clock), the threshold multiply, the clock add, the divide and
-# the logarithm. They are uniform within a cell, so one warp instruction
-# serves every cell that shares the warp: 1 in the one-cell kernels, 32 / W
-# in the grouped kernels (W lanes per cell). Algorithmic warp operations per
-# event = (K + 4) / cells per warp.
+# ---------------------------------------------------------------------------
+# Roofline of the window kernels: plain ALU lanes. The method's own work per
+# event (the per-event work list of the hot path), counted once per event in
+# 32-bit lane operations, whatever the kernel's layout:
+#   draw        one Philox4x32-10 block: 10 rounds x (2 mul.lo + 2 mul.hi +
+#               4 xor) + 9 key bumps x 2 = 98, and 6 to form u_t, u_c, j
+#   clock       the waiting time and the edge test: binary32 6 (log, divide,
+#               add, compare); binary64 18 (the 14-operation logarithm, the
+#               divide, the add, the compare)
+#   class       the class choice over K classes: binary64 2K (the ordered
+#               fused multiply-add chain and its compares), fixed point 3K
+#               (64-bit products and compares)
+#   member      the rank search in the chosen class's bit set: one popcount
+#               per 32-bit word of the set (a site class has ceil(n/32) words
+#               of a cell of n sites, a slot class 8 times that), a 5-step
+#               scan and a 10-operation select in the owner word; weighted by
+#               the fraction of events in slot classes
+#   update      4 operations (class, mask bit, two counts) per member whose
+#               class the event can change: 5 (spin flip), 3 (ring), 2 sites
+#               and 14 slots (ZGB), 25 sites and 40 slots (diffusion)
+# Peak: 152 SMs x 128 lanes x 2.07 GHz.
+ALU_PEAK_G = 152 * 128 * 2.07
 NCLASSES = {"ADSDES": 10, "ISING": 10, "DIFFUSION": 15, "ZGB": 4, "ISING1D": 6}
-# Peak (binary64): the nominal GB300 FP64 rate (1.25 TFLOP/s) as warp
-# instructions, 1.25e12 / (2 flops per FMA x 32 lanes) = 19.5 G warp-ops/s.
-FP64_WARP_OPS_PEAK_G = 1.25e12 / 64 / 1e9
-# Peak (binary32 clock): the warp-instruction issue rate, 152 SMs x 4
-# schedulers x 2.07 GHz.
-ISSUE_PEAK_G = 152 * 4 * 2.07
-# Measured dependent latency of one binary64 fused multiply-add on GB300
-# (cycles): the binary64 chain of K + 2 dependent operations per event is
-# the latency floor of the binary64 kernels.
-FP64_DEP_LATENCY_CYCLES = 64
+UPDATE_MEMBERS = {"ADSDES": 5, "ISING": 5, "ISING1D": 3, "ZGB": 16, "DIFFUSION": 65}
+SLOT_EVENT_FRACTION = {"ZGB": 0.5, "DIFFUSION": 0.5}
 
-# DRAM traffic per launch of the bench's kernel on the 1024^2 Ising workload
-# (bit-packed lattice) from one ncu capture (profiles/), valid only for the
-# kernel source it was taken on.
-PROFILED_TRAFFIC = {
-    "fs_group_kernel<ISING,double,packed,W=8>": {
-        "src": ["fskmc_group.cuh", "fskmc_device.cuh"], "bytes_per_launch": 186880,
-        "src_sha256": "196fdfa90747162fac54f84b80f0c113dcf7fbf75a77738ef23ecd32cccc9b96"},
+
+def algo_lane_ops_per_event(model, q, fp64):
+    K = NCLASSES[model]
+    words = -(-(q[0] * q[1]) // 32)
+    f = SLOT_EVENT_FRACTION.get(model, 0.0)
+    member = (1 - f) * words + f * 8 * words + 5 + 10
+    return 98 + 6 + (18 if fp64 else 6) + (2 * K if fp64 else 3 * K) + member + \
+        4 * UPDATE_MEMBERS[model]
+
+
+# ncu figures of the bench's kernels (profiles/), valid only for the kernel
+# source they were taken on: DRAM bytes per fractional window of the
+# workload and the issue-slot utilisation.
+PROFILED = {
+    ("fs_persistent_kernel<ZGB,float>", "zgb16384"): {
+        "src": ["fskmc_window.cu", "fskmc_device.cuh"], "dram_bytes_per_window": None,
+        "issue_active": None, "src_sha256": None},
 }
-
-
-def init_state(ctx, w, seed):
-    """The workload's initial state: the seeded Gaussian bump of species A on
-    an empty lattice where the workload names one, else Bernoulli coverage."""
-    if "bump" in w:
-        ctx.init_bump(seed, w["bump"]["amp"], w["bump"]["width"], 1)
-    else:
-        ctx.init_random(seed, w.get("coverage", 0.5))
-
-
-def stage_bytes_per_site(w):
-    """Algorithmic bytes one window moves per active site: the cell and its
-    one-site halo read, the cell written, (1 + 2/q)^2 + 1 sites, at one byte
-    per site or one bit per site when bit-packed."""
-    q = w["q"][0]
-    return ((1.0 + 2.0 / q) ** 2 + 1.0) / (8.0 if w.get("bitpacked") else 1.0)
 
 
 def src_sha(names):
@@ -177,68 +198,98 @@ def src_sha(names):
 def kernel_name(engine, model, fp64, packed, lanes):
     """The window kernel the bench's configuration launches."""
     grouped = lanes < 32
-    base = {("plain", False): "fs_window_kernel", ("persistent", False): "fs_persistent_kernel",
-            ("plain", True): "fs_group_kernel", ("persistent", True): "fs_group_persistent_kernel"}
+    base = {("PLAIN", False): "fs_window_kernel", ("PERSISTENT", False): "fs_persistent_kernel",
+            ("PLAIN", True): "fs_group_kernel", ("PERSISTENT", True): "fs_group_persistent_kernel"}
     args = [model, "double" if fp64 else "float"] + (["packed"] if packed else [])
     if grouped:
         args.append(f"W={lanes}")
     return f"{base[(engine, grouped)]}<{','.join(args)}>"
 
 
-def cpu_baseline(w, seconds):
-    """The oracle as it stands on a bounded sample of the workload: a 256x256
-    lattice (a ring of 8192 sites for the 1D model) of the same model, rates,
-    cell shape and schedule, advanced step by step until `seconds` of CPU
-    time. Events/s do not depend on the lattice size for the cell-by-cell
-    oracle (cost per event ~ cell size)."""
+def stage_bytes_per_site(w):
+    """Algorithmic bytes one window moves per active site: the cell and its
+    halo read, the cell written, (1 + 2 hw/q)^2 + 1 sites, at one byte per
+    site or one bit per site when bit-packed (hw = 2 for diffusion)."""
+    q = w["q"][0]
+    hw = 2 if w["model"] == "DIFFUSION" else 1
+    return ((1.0 + 2.0 * hw / q) ** 2 + 1.0) / (8.0 if w.get("bitpacked") else 1.0)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(w, threads):
+    """The oracle's run object on the workload's CPU sample: the same model,
+    rates, cells and schedule on a smaller lattice (the all-core form gets a
+    lattice with enough active cells for every thread), the same kind of
+    initial state."""
     import oracle
-    lx, ly = sample_shape(w)
-    run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
-                       oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
-    t0 = time.process_time()
-    steps = 0
-    while steps == 0 or time.process_time() - t0 < seconds:
+    lx, ly = cpu_sample(w, threads)
+    if "bump" in w:
+        init = oracle.init_bump(lx, ly, w["seed"], w["bump"]["amp"], lx / 8.0, 1)
+    else:
+        init = oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5))
+    return oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"], init), (lx, ly)
+
+
+def oracle_step(run, w, threads):
+    if threads > 1:
+        run.run_threads(w["scheme"], w["dt"], w["dt"], w["seed"], threads)
+    else:
         run.run(w["scheme"], w["dt"], w["dt"], w["seed"])
+
+
+def cpu_baseline(w, seconds, threads):
+    """The oracle as it stands on a bounded sample of the workload, one step
+    of dt at a time until `seconds` of wall time; events/s (the oracle's cost
+    per event depends on the cell size, not the lattice size)."""
+    run, (lx, ly) = oracle_sample(w, threads)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps == 0 or time.perf_counter() - t0 < seconds:
+        oracle_step(run, w, threads)
         steps += 1
-    dt = max(time.process_time() - t0, 1e-9)
-    return {"value": run.events / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"{lx}x{ly} lattice, same model/rates/cells/schedule, {steps} steps "
-                      f"of dt={w['dt']} ({run.events} events, {dt:.1f} s CPU, single thread)"}
-
-
-def ensemble_sample(w, reps, q):
-    """A single-lattice stand-in of the ensemble for the host-CPU oracle:
-    replica 0's rates, the ensemble's model, schedule and cells."""
-    return dict(model=w["model"], rates=reps[0]["rates"], q=tuple(q), scheme=w["scheme"], dt=w["dt"],
-                coverage=w["coverage"], seed=w["seed"])
+    dt = max(time.perf_counter() - t0, 1e-9)
+    return {"value": run.events / dt, "unit": "events/s", "cores": threads, "kind": "oracle",
+            "sample": f"{lx}x{ly} lattice, same model/rates/cells/schedule, {steps} steps of "
+                      f"dt={w['dt']} ({run.events} events in {dt:.1f} s wall), "
+                      + ("cells of each window over %d threads" % threads if threads > 1
+                         else "single thread")}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (all host cores, cells of each window
+    over threads) on the workload's CPU sample, one step of dt per bench
+    step. Rank 0 only."""
     w = WORKLOADS[args.workload]
     if args.workload == "ensemble512":
         from workloads import ensemble_replicas
         w = ensemble_sample(w, ensemble_replicas(w["n"], w["seed"]), (16, 16))
     if rank != 0:
         return
-    cb = None
+    threads = host_cores()
+    run, (lx, ly) = oracle_sample(w, threads)
     vals = []
-    import oracle
-    lx, ly = sample_shape(w)
-    run = oracle.FSRun(lx, ly, *w["q"], w["model"], w["rates"],
-                       oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5)))
     for i in range(args.warmup + args.steps):
         e0 = run.events
         t0 = time.perf_counter()
-        run.run(w["scheme"], w["dt"], w["dt"], w["seed"])
+        oracle_step(run, w, threads)
         t1 = time.perf_counter()
         if i >= args.warmup:
             vals.append(((run.events - e0), t1 - t0))
     ev = sum(v[0] for v in vals)
     tt = sum(v[1] for v in vals)
     value = ev / tt
-    cb = {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+    cb = {"value": value, "unit": "events/s", "cores": threads, "kind": "oracle",
           "sample": f"{lx}x{ly} lattice of the {args.workload} workload, one step of dt="
-                    f"{w['dt']} per bench step, single thread"}
+                    f"{w['dt']} per bench step, cells of each window over {threads} threads"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "events/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -250,11 +301,273 @@ def run_reference(args, rank, world):
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def ensemble_sample(w, reps, q):
+    """A single-lattice stand-in of the ensemble for the host-CPU oracle:
+    replica 0's rates, the ensemble's model, schedule and cells."""
+    return dict(model=w["model"], rates=reps[0]["rates"], q=tuple(q), scheme=w["scheme"], dt=w["dt"],
+                coverage=w["coverage"], seed=w["seed"])
+
+
+# ---------------------------------------------------------------------------
+# The GPU forms
+# ---------------------------------------------------------------------------
+def init_state(ctx, w, seed):
+    """The workload's initial state: the seeded Gaussian bump of species A on
+    an empty lattice where the workload names one, else Bernoulli coverage."""
+    if "bump" in w:
+        ctx.init_bump(seed, w["bump"]["amp"], w["bump"]["width"], 1)
+    else:
+        ctx.init_random(seed, w.get("coverage", 0.5))
+
+
+def make_ctx(F, w, form, stream, seed, args):
+    engine, clock = FORMS[form]
+    c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream,
+                  bitpacked=w.get("bitpacked", False))
+    c.set_engine(engine)
+    c.set_clock(clock)
+    if args.wpb:
+        c.set_warps_per_block(args.wpb)
+    c.set_task_order(args.order.upper())
+    c.set_cell_grouping({"auto": "AUTO", "on": True, "off": False}[args.grouping])
+    init_state(c, w, seed)
+    return c
+
+
+def time_form(F, w, form, stream, seed, args, flush, world, clk=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    context's stream (L2 flushed between steps, outside the events): one step
+    = fskmc_run over 10 dt + the observables. Returns the form's figures."""
+    import torch
+    ctx = make_ctx(F, w, form, stream, seed, args)
+    step_t = STEP_WINDOWS_DT * w["dt"]
+    for _ in range(args.warmup):
+        ctx.run(w["scheme"], w["dt"], step_t, seed)
+        ctx.observables(0, RMAX)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    barrier(world)
+    marks = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        ctx.run(w["scheme"], w["dt"], step_t, seed)
+        b.record(stream)
+        ctx.observables(0, RMAX)
+        c.record(stream)
+        marks.append((a, b, c))
+    torch.cuda.synchronize()
+    barrier(world)
+    st1 = ctx.stats()
+    step_ms = [a.elapsed_time(c) for a, b, c in marks]
+    run_ms = [a.elapsed_time(b) for a, b, c in marks]
+    info = ctx.info()
+    out = {"ctx": ctx, "events": st1["events"] - st0["events"], "windows": st1["windows"] - st0["windows"],
+           "ambiguous": st1["ambiguous"] - st0["ambiguous"], "check_failures": st1["check_failures"],
+           "timeouts": st1["timeouts"], "step_ms": step_ms, "run_ms": run_ms, "info": info}
+    t_ms = max_over_ranks(sum(step_ms), world)
+    out["events_all"] = sum_over_ranks(out["events"], world)
+    out["t_ms"] = t_ms
+    out["events_per_s"] = out["events_all"] / (t_ms / 1000.0)
+    return out
+
+
+def end_to_end(F, w, ctx, stream, seed, args, world):
+    """The same step through the C ABI with host buffers: every step copies
+    the lattice in from pinned host memory, runs, computes the observables
+    and copies the lattice out."""
+    import torch
+    lx, ly = w["lx"], w["ly"]
+    host = torch.empty(lx * ly, dtype=torch.uint8, pin_memory=True)
+    hnp = host.numpy()
+    ctx.get_state(0, hnp)
+    torch.cuda.synchronize()
+    e0 = ctx.stats()["events"]
+    step_t = STEP_WINDOWS_DT * w["dt"]
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state(hnp)
+        ctx.run(w["scheme"], w["dt"], step_t, seed)
+        ctx.observables(0, RMAX)
+        ctx.get_state(0, hnp)
+    torch.cuda.synchronize()
+    s = max_over_ranks(time.perf_counter() - t0, world)
+    ev = sum_over_ranks(ctx.stats()["events"] - e0, world)
+    return {"value": ev / s, "unit": "events/s", "h2d_bytes_per_step": lx * ly,
+            "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)}
+
+
+def observable_vector(ctx, model):
+    """Coverage of every state, energy (not for ZGB), G_x(1..4), G_y(1..4)."""
+    cov, en, pc = ctx.observables(0, 4)
+    names = [f"coverage[{s}]" for s in range(3 if model == "ZGB" else 2)]
+    vals = list(cov[:len(names)])
+    if model != "ZGB":
+        names.append("energy")
+        vals.append(en)
+    names += [f"Gx({r})" for r in range(1, 5)] + [f"Gy({r})" for r in range(1, 5)]
+    vals += list(pc[:4]) + list(pc[4:8])
+    return names, np.array(vals, np.float64)
+
+
+def dt_error(F, w, stream, runs, T, args):
+    """Per-observable dt-error at time T from the workload's initial state:
+    the plain binary64 form and the batched binary32 form at the workload's
+    dt against the binary64 form at dt/8 (the serial-SSA limit of the
+    splitting up to 1/64 of the error at dt for a second-order scheme, 1/8
+    for a first-order one), each over `runs` independent seeds; and the
+    binary32-minus-binary64 difference. Means and standard errors."""
+    res = {}
+    arms = {"fp64": ("plain_fp64", w["dt"]), "fp32": ("batched_fp32", w["dt"]),
+            "ref": ("plain_fp64", w["dt"] / 8)}
+    names = None
+    ambiguous = cellwin = 0
+    for arm, (form, dt) in arms.items():
+        vals = []
+        for s in range(runs):
+            c = make_ctx(F, w, form, stream, w["seed"] + 1000 + s, args)
+            c.run(w["scheme"], dt, T, w["seed"] + 1000 + s)
+            names, v = observable_vector(c, w["model"])
+            st = c.stats()
+            if arm != "fp32":
+                ambiguous += st["ambiguous"]
+                cellwin += st["windows"] * c.info()["cells"] // 2
+            vals.append(v)
+            c.close()
+        res[arm] = np.array(vals)
+    out = {"T": T, "runs_per_arm": runs, "reference": f"binary64 form at dt/8 = {w['dt'] / 8:g}",
+           "observables": {}}
+
+    def mse(a):
+        return a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(len(a))
+
+    m64, s64 = mse(res["fp64"])
+    m32, s32 = mse(res["fp32"])
+    mr, sr = mse(res["ref"])
+    for i, n in enumerate(names):
+        e64, se64 = m64[i] - mr[i], float(np.hypot(s64[i], sr[i]))
+        e32, se32 = m32[i] - mr[i], float(np.hypot(s32[i], sr[i]))
+        d, sd = m32[i] - m64[i], float(np.hypot(s32[i], s64[i]))
+        out["observables"][n] = {"value": float(mr[i]), "dt_error_fp64": float(e64), "se_fp64": se64,
+                                 "dt_error_fp32": float(e32), "se_fp32": se32,
+                                 "fp32_minus_fp64": float(d), "se_diff": sd,
+                                 "same_dt_error_within_3se": bool(abs(d) <= 3 * sd)}
+    out["all_within_3se"] = all(o["same_dt_error_within_3se"] for o in out["observables"].values())
+    out["ambiguous_cell_windows"] = int(ambiguous)
+    out["cell_windows"] = int(cellwin)
+    return out
+
+
+def run_workload(args, rank, world, local):
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    from paper_1105_4673_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = WORKLOADS[args.workload]
+    seed = rank_seed(w["seed"], rank)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    forms = [args.form] + ([args.compare] if args.compare not in ("none", args.form) else [])
+    if not args.no_variants:
+        forms += [f for f in FORMS if f not in forms]
+    res = {}
+    with ClockSampler(local) as clk:
+        for f in forms:
+            res[f] = time_form(F, w, f, stream, seed, args, flush, world)
+            if f != args.form:
+                res[f]["ctx"].close()
+    head = res[args.form]
+    e2e = end_to_end(F, w, head["ctx"], stream, seed, args, world)
+    info = head["info"]
+    head["ctx"].close()
+    if rank != 0:
+        return
+    dterr = dt_error(F, w, stream, args.dt_error_runs, args.dt_error_T, args) if args.dt_error_runs > 0 else None
+    engine, clock = FORMS[args.form]
+    fp64 = clock == "FP64"
+    lanes = info["lanes_per_cell"]
+    kname = kernel_name(engine, w["model"], fp64, bool(w.get("bitpacked")), lanes)
+    nwin_step = kernel_windows_per_step(F, w, STEP_WINDOWS_DT * w["dt"])
+    launches_per_step = 1 if engine == "PERSISTENT" else nwin_step
+    launch_s = float(np.mean(head["run_ms"])) / 1000.0 / launches_per_step
+    ev_launch = head["events"] / args.steps / launches_per_step
+    ops = algo_lane_ops_per_event(w["model"], w["q"], fp64)
+    achieved = ev_launch * ops / launch_s / 1e9
+    prof = PROFILED.get((kname, args.workload))
+    traffic = issue = None
+    if prof and prof["src_sha256"] and prof["src_sha256"] == src_sha(prof["src"]):
+        if prof["dram_bytes_per_window"]:
+            traffic = prof["dram_bytes_per_window"] * nwin_step / launches_per_step
+        issue = prof["issue_active"]
+    active_cells = info["cells"] // 2
+    comparisons = {}
+    for f, r in res.items():
+        comparisons[f] = {"events_per_s": r["events_per_s"], "ms_per_step": r["t_ms"] / args.steps,
+                          "engine": FORMS[f][0], "clock": FORMS[f][1],
+                          "lanes_per_cell": r["info"]["lanes_per_cell"],
+                          "warps_per_cta": r["info"]["warps_per_block"],
+                          "ambiguous_fraction": r["ambiguous"] / max(1, r["windows"] * active_cells),
+                          "check_failures": r["check_failures"], "timeouts": r["timeouts"]}
+    base = res.get(args.compare)
+    statement = None
+    if base is not None:
+        ratio = head["events_per_s"] / base["events_per_s"]
+        statement = (f"{args.form} {head['events_per_s']:.3e} events/s vs {args.compare} "
+                     f"{base['events_per_s']:.3e} events/s ({ratio:.2f}x) on {args.workload}, "
+                     f"{w['scheme']} dt={w['dt']}")
+        if dterr:
+            same = "within" if dterr["all_within_3se"] else "NOT within"
+            statement += (f"; the two forms' observables differ by {same} 3 SE at T={dterr['T']} "
+                          f"({dterr['runs_per_arm']} runs each)")
+    sb = stage_bytes_per_site(w)
+    out = {
+        "metric": METRIC, "value": head["events_per_s"], "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["t_ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32+u64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {w['lx']}x{w['ly']} {w['model']} {w['rates']} "
+                               f"q={w['q'][0]}x{w['q'][1]} {w['scheme']} dt={w['dt']}"
+                               + (" from a Gaussian bump of A" if "bump" in w else ""),
+                   "form": args.form, "engine": engine, "clock": clock,
+                   "step": f"{STEP_WINDOWS_DT * w['dt']:g} time units ({nwin_step} windows) through "
+                           "fskmc_run + observables (r <= 32)",
+                   "warps_per_cta": info["warps_per_block"], "lanes_per_cell": lanes,
+                   "storage": "1 bit/site" if w.get("bitpacked") else "1 byte/site",
+                   "l2": "flushed between timed steps (256 MiB buffer)"},
+        "comparison": comparisons,
+        "statement": statement,
+        "dt_error": dterr,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_G,
+                     "unit": "G lane-ops/s", "frac": achieved / ALU_PEAK_G, "traffic": traffic,
+                     "kernel": kname, "kernel_ms_avg": launch_s * 1000,
+                     "launches_per_step": launches_per_step, "events_per_launch": ev_launch,
+                     "algorithmic_lane_ops_per_event": ops,
+                     "issue_active_ncu": issue,
+                     "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz (plain ALU lanes; the "
+                                  "path has no dense contraction)",
+                     "hbm_note": f"{sb:.2f} algorithmic bytes per active site per window; "
+                                 f"{sb * active_cells * w['q'][0] * w['q'][1] * nwin_step / launches_per_step / launch_s / 1e9:.1f}"
+                                 " GB/s of algorithmic traffic: HBM is not the bound"},
+        "cpu_baseline": cpu_baseline(w, args.cpu_seconds, host_cores()),
+        "cpu_baseline_1core": cpu_baseline(w, args.cpu_seconds, 1),
+        "e2e": e2e,
+        "gpu_launches": args.steps * (launches_per_step + 1),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def run_ensemble(args, rank, world, local):
     """The batched ensemble (512 replicas of uneven size and rates) advanced
     in one persistent, graph-launched kernel per step; one step = 10 dt of
     physical time for every replica. Cell size and warps per block come from
-    the library's autotuner."""
+    the library's autotuner. Beside it: the same replicas one at a time
+    through the plain binary64 form."""
     import torch
 
     import paper_1105_4673_gb300 as F
@@ -316,18 +629,18 @@ def run_ensemble(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_events = sum_over_ranks(b.stats()["events"] - e_ev0, world)
-    if rank != 0:
-        b.close()
-        return
-    fp64 = clock == "FP64"
     lanes = b.info()["lanes_per_cell"]
-    cells_per_warp = 32 // lanes if lanes < 32 else 1
-    ops = NCLASSES[w["model"]] + 4
+    cells = b.info()["cells"]
+    b.close()
+    if rank != 0:
+        return
+    one_at_a_time = ensemble_one_at_a_time(F, reps, w, stream, seed, q)
+    fp64 = clock == "FP64"
     k_avg_s = t_ms / 1000.0 / args.steps
-    achieved = events / args.steps * ops / cells_per_warp / k_avg_s / 1e9
-    peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
+    ops = algo_lane_ops_per_event(w["model"], q, fp64)
+    achieved = events / args.steps * ops / k_avg_s / 1e9
     nbytes = sum(r["lx"] * r["ly"] for r in reps)
-    cb = cpu_baseline(ensemble_sample(w, reps, q), args.cpu_seconds)
+    cb = cpu_baseline(ensemble_sample(w, reps, q), args.cpu_seconds, host_cores())
     cb["sample"] = "replica 0's rates and the autotuned cells: " + cb["sample"]
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
@@ -338,310 +651,195 @@ def run_ensemble(args, rank, world, local):
                    "step": f"{step_t:g} time units for every replica, one persistent launch",
                    "clock": args.clock, "engine": "persistent", "cell": f"{q[0]}x{q[1]}" + ("" if args.cell else " (autotuned)"),
                    "warps_per_cta": wpb, "lanes_per_cell": lanes, "sites": nbytes,
-                   "cells": b.info()["cells"], "l2": "flushed between timed steps"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "G fp64 warp-ops/s" if fp64 else "G warp-ops/s", "frac": achieved / peak,
-                     "traffic": None,
-                     "kernel": kernel_name("persistent", w["model"], fp64, False, lanes),
+                   "cells": cells, "l2": "flushed between timed steps"},
+        "comparison": {"one_replica_at_a_time_plain_fp64": one_at_a_time},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_G,
+                     "unit": "G lane-ops/s", "frac": achieved / ALU_PEAK_G, "traffic": None,
+                     "kernel": kernel_name("PERSISTENT", w["model"], fp64, False, lanes),
                      "kernel_ms_avg": k_avg_s * 1000, "launches": args.steps,
-                     "events_per_launch": events / args.steps, "algorithmic_ops_per_event": ops,
-                     "cells_per_warp": cells_per_warp,
-                     "algorithmic_warp_ops_per_event": ops / cells_per_warp,
-                     "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
-                                   if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz")},
+                     "events_per_launch": events / args.steps, "algorithmic_lane_ops_per_event": ops,
+                     "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz"},
         "cpu_baseline": cb,
         "e2e": {"value": e2e_events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }), flush=True)
-    b.close()
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_setup(args.gpus)
-    if args.impl == "reference":
-        run_reference(args, rank, world)
-        return
-    if args.workload == "ensemble512":
-        from paper_1105_4673_gb300 import build as B
-        B.build()
-        run_ensemble(args, rank, world, local)
-        return
+def ensemble_one_at_a_time(F, reps, w, stream, seed, q, T=1.0):
+    """The ensemble's baseline: the same replicas advanced one at a time,
+    each through its own plain binary64 context (one launch per window per
+    replica), for T time units after 1 time unit of warm-up."""
     import torch
-
-    import paper_1105_4673_gb300 as F
-    from paper_1105_4673_gb300 import build as B
-    B.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    w = WORKLOADS[args.workload]
-    lx, ly = w["lx"], w["ly"]
-    seed = rank_seed(w["seed"], rank)
-    ctx = F.Context(lx, ly, w["model"], w["rates"], w["q"], stream=stream,
-                    bitpacked=w.get("bitpacked", False))
-    ctx.set_engine(args.engine.upper())
-    ctx.set_clock(args.clock.upper())
-    if args.wpb:
-        ctx.set_warps_per_block(args.wpb)
-    ctx.set_task_order(args.order.upper())
-    ctx.set_cell_grouping({"auto": "AUTO", "on": True, "off": False}[args.grouping])
-    init_state(ctx, w, seed)
-    step_t = STEP_WINDOWS_DT * w["dt"]
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
-    def step(kernel_events=None):
-        # plain engine: one window-kernel launch per window, each bracketed by
-        # events on the context's stream; persistent: one launch per run
-        if args.engine == "plain":
-            col, hh = F.schedule(w["scheme"], w["dt"], step_t, seed, 0, ctx.window_index)
-            for c, h in zip(col, hh):
-                if kernel_events is not None:
-                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    ctx.window(int(c), float(h), seed)
-                    b.record(stream)
-                    kernel_events.append((a, b))
-                else:
-                    ctx.window(int(c), float(h), seed)
-        else:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ctx.run(w["scheme"], w["dt"], step_t, seed)
-            b.record(stream)
-            if kernel_events is not None:
-                kernel_events.append((a, b))
-        return ctx.observables(0, RMAX)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    ev0 = ctx.stats()["events"]
-    barrier(world)
-    torch.cuda.synchronize()
-    kev = []
-    step_times = []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()  # L2 flush between timed steps (outside the step's events)
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            step(kev)
-            s1.record(stream)
-            step_times.append((s0, s1))
-        torch.cuda.synchronize()
-    barrier(world)
-    events = ctx.stats()["events"] - ev0
-    t_ms = sum(a.elapsed_time(b) for a, b in step_times)
-    t_ms = max_over_ranks(t_ms, world)
-    events_all = sum_over_ranks(events, world)
-    kernel_ms = [a.elapsed_time(b) for a, b in kev]
-    value = events_all / (t_ms / 1000.0)
-
-    # end to end through the C ABI with host buffers: H2D of the state from
-    # pinned memory, the step, D2H of the state and the observables
-    host = torch.empty(lx * ly, dtype=torch.uint8, pin_memory=True)
-    hnp = host.numpy()
-    ctx.get_state(0, hnp)
-    torch.cuda.synchronize()
-    e_ev0 = ctx.stats()["events"]
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx.set_state(hnp)
-        ctx.run(w["scheme"], w["dt"], step_t, seed)
-        ctx.observables(0, RMAX)
-        ctx.get_state(0, hnp)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_events = sum_over_ranks(ctx.stats()["events"] - e_ev0, world)
-
-    variants = {}
-    if not args.no_variants and rank == 0:
-        variants = measure_variants(F, w, stream, seed, steps=max(2, args.steps // 2))
-
-    if rank != 0:
-        ctx.close()
-        return
-    cs = clk.summary()
-    k_events_per_launch = events / max(len(kernel_ms), 1)
-    k_avg_s = float(np.mean(kernel_ms)) / 1000.0
-    lanes = ctx.info()["lanes_per_cell"]
-    cells_per_warp = 32 // lanes if lanes < 32 else 1
-    ops_per_event = NCLASSES[w["model"]] + 4
-    warp_ops_per_event = ops_per_event / cells_per_warp
-    achieved = k_events_per_launch * warp_ops_per_event / k_avg_s / 1e9
-    fp64 = args.clock == "fp64"
-    peak = FP64_WARP_OPS_PEAK_G if fp64 else ISSUE_PEAK_G
-    kname = kernel_name(args.engine, w["model"], fp64, bool(w.get("bitpacked")), lanes)
-    traffic = None
-    prof = PROFILED_TRAFFIC.get(kname)
-    if prof and args.workload == "ising1024" and prof["src_sha256"] == src_sha(prof["src"]):
-        traffic = prof["bytes_per_launch"]
-    # the critical path: the slowest cell's events in the last window set the
-    # window's duration; cycles per event of that cell vs the binary64 floor
-    wl_max = int(ctx.workload(0).max()) if args.engine == "plain" else 0
-    sm_mhz = clk.summary().get("sm_mhz") or 2070.0
-    cb = cpu_baseline(w, args.cpu_seconds)
-    out = {
-        "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if fp64 else "f32+u64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {lx}x{ly} {w['model']} betaJ="
-                               f"{w['rates'].get('betaJ')} q={w['q'][0]} {w['scheme']} dt={w['dt']}",
-                   "step": f"{step_t:g} time units ({kernel_windows_per_step(F, w, step_t)} windows) "
-                           "+ observables",
-                   "clock": args.clock, "engine": args.engine,
-                   "warps_per_cta": ctx.info()["warps_per_block"],
-                   "lanes_per_cell": ctx.info()["lanes_per_cell"], "task_order": args.order,
-                   "storage": "1 bit/site" if w.get("bitpacked") else "1 byte/site",
-                   "l2": "flushed between timed steps"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "G fp64 warp-ops/s" if fp64 else "G warp-ops/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "kernel": kname,
-                     "kernel_ms_avg": k_avg_s * 1000, "launches": len(kernel_ms),
-                     "events_per_launch": k_events_per_launch,
-                     "algorithmic_ops_per_event": ops_per_event,
-                     "cells_per_warp": cells_per_warp,
-                     "algorithmic_warp_ops_per_event": warp_ops_per_event,
-                     "peak_note": ("derived: nominal 1.25 TFLOP/s FP64 / 64 flops per warp FMA"
-                                   if fp64 else "derived: 152 SMs x 4 schedulers x 2.07 GHz") +
-                                  f"; HBM is not the bound ({stage_bytes_per_site(w):.2f} B per "
-                                  "active site per window)",
-                     "critical_path": None if not wl_max else {
-                         "slowest_cell_events": wl_max,
-                         "cycles_per_event": k_avg_s * sm_mhz * 1e6 / wl_max,
-                         "binary64_floor_cycles_per_event":
-                             (NCLASSES[w["model"]] + 2) * FP64_DEP_LATENCY_CYCLES if fp64 else None}},
-        "cpu_baseline": cb,
-        "e2e": {"value": e2e_events / e2e_s, "unit": "events/s",
-                "h2d_bytes_per_step": lx * ly, "d2h_bytes_per_step": lx * ly + 8 * (4 + 2 * RMAX)},
-        "gpu_launches": len(kernel_ms) + args.steps,
-        "clocks": cs,
-        "variants": variants,
-    }
-    print(json.dumps(out), flush=True)
-    ctx.close()
-
-
-def measure_variants(F, w, stream, seed, steps):
-    """The same workload through the persistent engine (one graph-launched
-    kernel per run) with binary64 and binary32 window clocks; the 512-replica
-    ensemble in one persistent launch per run (binary32 clock, the batched
-    form); and the binary32-vs-binary64 difference of the observables."""
-    import torch
-    res = {}
-    res["ensemble512_persistent_fp32"] = ensemble_rate(F, stream, "FP32")
-    res["ensemble512_persistent_fp64"] = ensemble_rate(F, stream, "FP64")
-    res["fp32_vs_fp64"] = clock_error(F, stream, w)
-    forms = [("PERSISTENT", "FP64", "AUTO"), ("PERSISTENT", "FP32", "AUTO"), ("PLAIN", "FP32", "AUTO")]
-    if _group_width_default(F, w) < 32:  # the same workload with one cell per warp
-        forms += [("PLAIN", "FP64", False)]
-    for engine, clock, grouped in forms:
-        c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"], stream=stream,
-                      bitpacked=w.get("bitpacked", False))
-        c.set_engine(engine)
-        c.set_clock(clock)
-        c.set_cell_grouping(grouped)
-        init_state(c, w, seed)
-        step_t = STEP_WINDOWS_DT * w["dt"]
-        c.run(w["scheme"], w["dt"], step_t, seed)
+    ev = 0
+    ms = 0.0
+    for r, rp in enumerate(reps):
+        c = F.Context(rp["lx"], rp["ly"], w["model"], rp["rates"], q, stream=stream)
+        c.set_replica_id(r)
+        c.init_random(seed, w["coverage"])
+        c.run(w["scheme"], w["dt"], 1.0, seed)
         torch.cuda.synchronize()
         e0 = c.stats()["events"]
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(steps):
-            c.run(w["scheme"], w["dt"], step_t, seed)
+        c.run(w["scheme"], w["dt"], T, seed)
         b.record(stream)
         torch.cuda.synchronize()
-        ev = c.stats()["events"] - e0
-        key = f"{engine.lower()}_{clock.lower()}" + ("" if grouped else "_one_cell_per_warp")
-        res[key] = {"events_per_s": ev / (a.elapsed_time(b) / 1000), "events": ev,
-                    "lanes_per_cell": c.info()["lanes_per_cell"]}
+        ev += c.stats()["events"] - e0
+        ms += a.elapsed_time(b)
         c.close()
-    return res
+    return {"events_per_s": ev / (ms / 1000.0), "events": ev, "T": T, "replicas": len(reps)}
 
 
-def _group_width_default(F, w):
-    """Lanes per cell the library picks for the workload's cells."""
-    c = F.Context(w["lx"], w["ly"], w["model"], w["rates"], w["q"],
-                  bitpacked=w.get("bitpacked", False))
-    n = c.info()["lanes_per_cell"]
+def time_average(F, w, form, stream, seed, dt, scheme, burn, T, args, every=1.0):
+    """Observables averaged over samples every `every` time units in
+    [burn, T] of one run from the workload's initial state."""
+    c = make_ctx(F, w, form, stream, seed, args)
+    c.run(scheme, dt, burn, seed)
+    acc = []
+    t = burn
+    names = None
+    while t < T - 1e-9:
+        c.run(scheme, dt, every, seed)
+        t += every
+        names, v = observable_vector(c, w["model"])
+        acc.append(v)
     c.close()
-    return n
+    return names, np.mean(np.array(acc), axis=0)
 
 
-def ensemble_rate(F, stream, clock, T=5.0):
-    """Events/s of the 512-replica ensemble (sides 64..512, betaJ in
-    [0.2, 0.8], ka/kd log-uniform) advanced by T in one persistent run."""
+def fit_order(dts, errs, ses):
+    """Weighted least-squares fit of log|e| = log C + p log dt (weights from
+    the standard errors); returns p and its standard error."""
+    x = np.log(np.asarray(dts))
+    y = np.log(np.abs(np.asarray(errs)))
+    sy = np.asarray(ses) / np.maximum(np.abs(np.asarray(errs)), 1e-300)
+    wgt = 1.0 / np.maximum(sy, 1e-12) ** 2
+    A = np.stack([np.ones_like(x), x], axis=1)
+    cov = np.linalg.inv(A.T @ (A * wgt[:, None]))
+    beta = cov @ (A.T @ (wgt * y))
+    return float(beta[1]), float(np.sqrt(cov[1, 1]))
+
+
+def study_weak_order(args):
+    """Weak-error order of Lie and Strang splitting (Eqs. error, error2) on
+    the 1024^2 Ising workload: time-averaged observables (samples every time
+    unit over [T/2, T]) at dt in {1, 1/2, 1/4, 1/8} against the same
+    average at dt = 1/32 (the serial-SSA limit of the splitting, up to 1/32
+    of the Lie error at dt = 1 and 1/1024 of the Strang error), several
+    independent runs per point; the error's order by a weighted log-log fit
+    over the points resolved beyond 3 standard errors."""
     import torch
-    from workloads import ensemble_replicas
-    w = WORKLOADS["ensemble512"]
-    reps = ensemble_replicas(w["n"], w["seed"])
-    q, wpb, _ = F.autotune(reps, w["model"], w["scheme"], w["dt"], clock=clock,
-                           engine="PERSISTENT", coverage=w["coverage"], seed=w["seed"],
-                           stream=stream)
-    b = F.Context(model=w["model"], q=q, batch=reps, stream=stream)
-    b.set_engine("PERSISTENT")
-    b.set_warps_per_block(wpb)
-    b.set_clock(clock)
-    b.init_random(w["seed"], w["coverage"])
-    b.run(w["scheme"], w["dt"], 1.0, w["seed"])
-    torch.cuda.synchronize()
-    e0 = b.stats()["events"]
-    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    b.run(w["scheme"], w["dt"], T, w["seed"])
-    c.record(stream)
-    torch.cuda.synchronize()
-    ev = b.stats()["events"] - e0
-    out = {"events_per_s": ev / (a.elapsed_time(c) / 1000), "events": ev, "replicas": len(reps),
-           "sites": int(sum(r["lx"] * r["ly"] for r in reps)), "T": T, "cells": b.info()["cells"],
-           "autotuned": {"q": q[0], "warps_per_block": wpb}}
-    b.close()
-    return out
+
+    import paper_1105_4673_gb300 as F
+    stream = torch.cuda.current_stream()
+    w = dict(WORKLOADS["ising1024"])
+    if args.betaJ is not None:
+        w["rates"] = dict(w["rates"], betaJ=args.betaJ)
+    runs, T = max(2, args.dt_error_runs), 200.0
+    burn = T / 2
+    dts = [1.0, 0.5, 0.25, 0.125]
+
+    def arm(scheme, dt):
+        vals = [time_average(F, w, "plain_fp64", stream, w["seed"] + 100 + s, dt, scheme, burn, T, args)
+                for s in range(runs)]
+        names = vals[0][0]
+        a = np.array([v[1] for v in vals])
+        return names, a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(runs)
+
+    t0 = time.time()
+    names, ref_m, ref_s = arm("STRANG", 1.0 / 32)
+    out = {"workload": f"ising1024 betaJ={w['rates']['betaJ']}", "T": T, "average_over": [burn, T],
+           "runs_per_point": runs, "reference": "Strang at dt = 1/32", "schemes": {}}
+    for scheme in ("LIE", "STRANG"):
+        rows = {}
+        for dt in dts:
+            _, m, s = arm(scheme, dt)
+            rows[dt] = (m - ref_m, np.hypot(s, ref_s))
+        per_obs = {}
+        for i, n in enumerate(names):
+            e = [float(rows[d][0][i]) for d in dts]
+            se = [float(rows[d][1][i]) for d in dts]
+            ok = [j for j in range(len(dts)) if abs(e[j]) > 3 * se[j]]
+            fit = fit_order([dts[j] for j in ok], [e[j] for j in ok], [se[j] for j in ok]) if len(ok) >= 2 else None
+            per_obs[n] = {"reference_value": float(ref_m[i]), "error": e, "se": se,
+                          "resolved_points": [dts[j] for j in ok],
+                          "order": None if fit is None else fit[0], "order_se": None if fit is None else fit[1]}
+        out["schemes"][scheme] = {"dt": dts, "observables": per_obs}
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out), flush=True)
 
 
-def clock_error(F, stream, w, n=64, L=128, T=10.0):
-    """Binary32 minus binary64 clock, per observable, over n independent
-    replicas of an L x L lattice of the workload's model (mean difference and
-    its standard error), and each form's dt-error estimate against dt/16."""
+def study_weak_order_replicas(args, L=32, q=2, M=8192, batches=4, T=1.0):
+    """Weak-error order resolved on many small replicas (cells of 2 x 2 sites
+    put every site on a cell edge, where the splitting error lives): M
+    replicas of an L x L Ising lattice, advanced to time T in one persistent binary64 launch per batch;
+    the replica mean of the energy, coverage and G(1) at T (each batch's
+    replicas start from their own Bernoulli(1/2) draw, the same draws in
+    every arm) for Lie and
+    Strang at dt in {1, 1/2, 1/4, 1/8} against Strang at dt = 1/32, and the
+    order fitted over the points resolved beyond 3 standard errors."""
     import torch
-    shape = (L * L, 1) if w["model"] == "ISING1D" else (L, L)
-    reps = [dict(lx=shape[0], ly=shape[1], rates=w["rates"]) for _ in range(n)]
 
-    def run(clock, dt, seed):
-        b = F.Context(model=w["model"], q=w["q"], batch=reps, stream=stream)
-        b.set_engine("PERSISTENT")
-        b.set_clock(clock)
-        b.init_random(seed, w.get("coverage", 0.5))
-        b.run(w["scheme"], dt, T, seed)
-        obs = []
-        for r in range(n):
-            cov, en, _ = b.observables(r, 1)
-            obs.append([cov[1], en])
-        obs = np.array(obs)
-        b.close()
-        return obs
+    import paper_1105_4673_gb300 as F
+    stream = torch.cuda.current_stream()
+    betaJ = 0.6 if args.betaJ is None else args.betaJ
+    rates = dict(ka=1.0, kd=1.0, betaJ=betaJ)
+    dts = [1.0, 0.5, 0.25, 0.125]
 
-    out = {"replicas": n, "lattice": f"{shape[0]}x{shape[1]}", "T": T, "dt": w["dt"]}
-    f64 = run("FP64", w["dt"], 101)
-    f32 = run("FP32", w["dt"], 202)
-    ref = run("FP64", w["dt"] / 16, 303)
-    for j, name in enumerate(("coverage", "energy")):
-        d = f32[:, j].mean() - f64[:, j].mean()
-        se = float(np.sqrt(f32[:, j].var(ddof=1) / n + f64[:, j].var(ddof=1) / n))
-        e64 = f64[:, j].mean() - ref[:, j].mean()
-        e32 = f32[:, j].mean() - ref[:, j].mean()
-        se_r = float(np.sqrt(f64[:, j].var(ddof=1) / n + ref[:, j].var(ddof=1) / n))
-        out[name] = {"fp32_minus_fp64": float(d), "se": se, "within_3se": bool(abs(d) < 3 * se),
-                     "dt_error_fp64": float(e64), "dt_error_fp32": float(e32), "dt_error_se": se_r}
-    torch.cuda.synchronize()
-    return out
+    def arm(scheme, dt):
+        vals = []
+        for b in range(batches):
+            reps = [dict(lx=L, ly=L, rates=rates) for _ in range(M)]
+            c = F.Context(model="ISING", q=(q, q), batch=reps, stream=stream)
+            c.set_engine("PERSISTENT")
+            c.init_random(4242 + b, 0.5)
+            c.run(scheme, dt, T, 777 + 1000 * b)
+            for r in range(M):
+                cov, en, pc = c.observables(r, 1)
+                vals.append([en, cov[1], pc[0]])
+            c.close()
+        a = np.array(vals)
+        return a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(len(a))
+
+    t0 = time.time()
+    ref_m, ref_s = arm("STRANG", 1.0 / 32)
+    names = ["energy", "coverage", "Gx(1)"]
+    out = {"workload": f"{M * batches} replicas of {L}x{L} ISING betaJ={betaJ}, {q}x{q} cells, T={T}, "
+                       "from Bernoulli(1/2) states", "reference": "Strang at dt = 1/32", "schemes": {}}
+    for scheme in ("LIE", "STRANG"):
+        rows = [arm(scheme, dt) for dt in dts]
+        per = {}
+        for i, n in enumerate(names):
+            e = [float(m[i] - ref_m[i]) for m, _ in rows]
+            se = [float(np.hypot(s[i], ref_s[i])) for _, s in rows]
+            ok = [j for j in range(len(dts)) if abs(e[j]) > 3 * se[j]]
+            fit = fit_order([dts[j] for j in ok], [e[j] for j in ok], [se[j] for j in ok]) if len(ok) >= 2 else None
+            per[n] = {"reference_value": float(ref_m[i]), "error": e, "se": se,
+                      "resolved_points": [dts[j] for j in ok],
+                      "order": None if fit is None else fit[0], "order_se": None if fit is None else fit[1]}
+        out["schemes"][scheme] = {"dt": dts, "observables": per}
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out), flush=True)
+
+
+def study_clock_error(args):
+    """Binary32 minus binary64 window clock, per observable, on the
+    workload's own lattice and schedule: several independent runs of each
+    form to time 10 dt * 10 from the initial state, and each form's dt-error
+    against the binary64 form at dt/8."""
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    T = STEP_WINDOWS_DT * w["dt"] * 10
+    t0 = time.time()
+    out = dt_error(F, w, stream, max(2, args.dt_error_runs), T, args)
+    out["workload"] = args.workload
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out), flush=True)
 
 
 def kernel_windows_per_step(F, w, step_t):
@@ -680,6 +878,29 @@ def sum_over_ranks(x, world):
 def rank_seed(base, rank):
     """Each rank simulates its own independent lattice (weak scaling)."""
     return base + 7919 * rank
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    from paper_1105_4673_gb300 import build as B
+    B.build()
+    if args.study == "weak-order":
+        study_weak_order(args)
+        return
+    if args.study == "weak-order-replicas":
+        study_weak_order_replicas(args)
+        return
+    if args.study == "clock-error":
+        study_clock_error(args)
+        return
+    if args.workload == "ensemble512":
+        run_ensemble(args, rank, world, local)
+        return
+    run_workload(args, rank, world, local)
 
 
 if __name__ == "__main__":

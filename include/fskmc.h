@@ -209,6 +209,35 @@ typedef enum {
 } fskmc_task_order;
 fskmc_status fskmc_set_task_order(fskmc_ctx *ctx, fskmc_task_order order);
 
+/*
+ * Nested (two-level) decomposition, Section 5 (Eq. sublatt2, Eq. opdecomp2).
+ * The lattice is a checkerboard of super-cells super_cell.qx x super_cell.qy
+ * (colours E/O); each super-cell is a checkerboard of the context's cells
+ * (here: sub-cells), so L^E_m = L^EE_m + L^EO_m. With nesting on, fskmc_run
+ * and fskmc_window run the outer schedule over the super-cell colours
+ * (window length h as without nesting), and inside every outer window each
+ * super-cell of that colour runs n_inner inner steps of the inner schedule
+ * over its sub-cell colours with step d = h / n_inner: LIE EE(d) EO(d),
+ * STRANG EE(d/2) EO(d) EE(d/2). Each inner window is a fractional window of
+ * the sub-cells of one inner colour (their own serial SSA, neighbours
+ * frozen); its draws use window index w * ninner + j (w the outer window
+ * index, j the inner window within it, ninner = 2 or 3 times n_inner) and
+ * the sub-cell's id. On the GPU a super-cell is one thread block kept in
+ * shared memory for the whole outer window, its sub-cells the block's warps;
+ * one launch per outer window (the engine setting does not apply); results
+ * are those of the CPU oracle's nested run bit for bit (binary64 clock).
+ * fskmc_stats counts inner windows; the window index counts outer windows.
+ *
+ * super_cell {0, 0}: nesting off (the default). EINVAL: a model other than
+ * ADSDES and ISING_ARRHENIUS; super-cell sides not multiples of twice the
+ * cell sides; lattice sides not multiples of twice the super-cell sides;
+ * inner not LIE or STRANG; n_inner < 1; a bit-packed lattice with
+ * super_cell.qx not a multiple of 32; a super-cell too large for one block's
+ * shared memory.
+ */
+fskmc_status fskmc_set_nesting(fskmc_ctx *ctx, fskmc_cell_shape super_cell, fskmc_scheme inner,
+                               int32_t n_inner);
+
 /* Persistent engine: how many times a cell polls a neighbour's progress
    before giving up (default 2^20; polls back off to one per 4 us, so about
    4 s). A run whose wait gives up returns FSKMC_ETIMEOUT and leaves the

@@ -37,7 +37,7 @@ EXPORTS = [
     "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_exact_edge_checks", "fskmc_workload", "fskmc_sync",
     "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_selftest_log",
-    "fskmc_schedule",
+    "fskmc_schedule", "fskmc_set_nesting",
 ]
 NOALLOC_MAX_RMAX = 256
 
@@ -89,6 +89,7 @@ def lib():
             "fskmc_set_edge_screen": ([vp, C.c_int32], C.c_int),
             "fskmc_set_spin_limit": ([vp, C.c_uint32], C.c_int),
             "fskmc_set_task_order": ([vp, C.c_int], C.c_int),
+            "fskmc_set_nesting": ([vp, CellShape, C.c_int, C.c_int32], C.c_int),
             "fskmc_info": ([vp, C.POINTER(C.c_int32)], C.c_int),
             "fskmc_init_random": ([vp, C.c_uint64, C.c_double], C.c_int),
             "fskmc_init_bump": ([vp, C.c_uint64, C.c_double, C.c_double, C.c_int32], C.c_int),
@@ -227,6 +228,15 @@ class Context:
     def set_task_order(self, order):
         o = ORDERS[order] if isinstance(order, str) else int(order)
         _check(lib().fskmc_set_task_order(self.h, o), self.h)
+
+    def set_nesting(self, super_cell, inner="LIE", n_inner: int = 1):
+        """Nested two-level scheme (Section 5): super-cells of shape
+        super_cell, each a checkerboard of the context's cells, with n_inner
+        inner steps of the inner schedule per outer window; None turns it
+        off."""
+        shape = CellShape(*(super_cell if super_cell else (0, 0)))
+        s = SCHEMES[inner] if isinstance(inner, str) else int(inner)
+        _check(lib().fskmc_set_nesting(self.h, shape, s, n_inner), self.h)
 
     def info(self) -> dict:
         out = (C.c_int32 * 6)()

@@ -50,6 +50,8 @@ struct fskmc_ctx {
     int32_t *d_order_scratch = nullptr;  // bucket histograms and cursors
     cudaStream_t stream = nullptr;
     fskmc::PersistentState *pers = nullptr;
+    int nest_qx = 0, nest_qy = 0;        // super-cell shape of the nested scheme (0: off)
+    int nest_inner = 0, nest_n = 1;      // inner schedule (LIE / STRANG) and inner steps
     std::string err;
 };
 
@@ -543,6 +545,58 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
     return FSKMC_OK;
 }
 
+// Warps per block of the nested kernel: one per active sub-cell of a
+// super-cell's inner window, at most 16, fewer if shared memory runs out.
+int nested_wpb(const fskmc_ctx *c)
+{
+    const int nact = (c->nest_qx / c->qx) * (c->nest_qy / c->qy) / 2;
+    int wpb = std::min(nact, 16);
+    while (wpb > 1 && fskmc::nested_smem(c->model, c->nest_qx, c->nest_qy, c->qx, c->qy, wpb) > 227 * 1024)
+        --wpb;
+    return wpb;
+}
+
+// The nested scheme (fskmc_set_nesting): every outer window of the
+// schedule runs the inner schedule inside each super-cell of its colour,
+// one launch per outer window and replica.
+fskmc_status nested_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sched, uint64_t seed)
+{
+    const size_t nw = sched[0].size();
+    const uint64_t ninner = (uint64_t)(c->nest_inner == FSKMC_LIE ? 2 : 3) * (uint64_t)c->nest_n;
+    if ((c->w + nw) * ninner > 0xFFFFFFFFull)
+        return fail(c, FSKMC_EINVAL, "nested run: inner window index beyond 2^32");
+    const int wpb = nested_wpb(c);
+    const int super_bytes = ((c->nest_qx + 2) * (c->nest_qy + 2) + 15) & ~15;
+    for (size_t i = 0; i < nw; ++i) {
+        for (int r = 0; r < c->nrep; ++r) {
+            const Win &win = sched[sched.size() == 1 ? 0 : r][i];
+            const Replica &R = c->reps[r];
+            fskmc::NestedArgs a;
+            a.reps = c->d_reps;
+            a.rep_index = r;
+            a.geom = fskmc::make_geom(c->qx, c->qy);
+            a.Qx = c->nest_qx;
+            a.Qy = c->nest_qy;
+            a.colour = win.colour;
+            a.w0 = (uint32_t)((c->w + i) * ninner);
+            a.inner = c->nest_inner == FSKMC_LIE ? 0 : 1;
+            a.ninner = (int32_t)ninner;
+            a.d = win.h / (double)c->nest_n;
+            a.dhalf = a.d * 0.5;
+            a.seed = seed;
+            a.lat = c->d_lat[c->cur];
+            a.workload = c->d_workload;
+            a.counters = c->d_counters;
+            a.packed = c->packed ? 1 : 0;
+            a.screen = c->edge_screen;
+            a.super_bytes = super_bytes;
+            const int nsuper = (R.lx / c->nest_qx) * (R.ly / c->nest_qy) / 2;
+            CK(c, fskmc::launch_nested(c->model, c->clock == FSKMC_CLOCK_FP32, a, nsuper, wpb, c->stream));
+        }
+    }
+    return FSKMC_OK;
+}
+
 // Byte-per-site view of a replica's lattice for the init/copy kernels: the
 // replica's own storage, or the staging buffer of a packed context.
 uint8_t *byte_view(fskmc_ctx *c, int r)
@@ -651,6 +705,36 @@ fskmc_status fskmc_set_edge_screen(fskmc_ctx *c, int32_t on)
     if (!c) return FSKMC_EINVAL;
     if (on != 0 && on != 1) return fail(c, FSKMC_EINVAL, "edge screen must be 0 (off) or 1 (on)");
     c->edge_screen = on;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_nesting(fskmc_ctx *c, fskmc_cell_shape sup, fskmc_scheme inner, int32_t n_inner)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (sup.qx == 0 && sup.qy == 0) {
+        c->nest_qx = c->nest_qy = 0;
+        return FSKMC_OK;
+    }
+    if (c->model != fskmc::ADSDES && c->model != fskmc::ISING)
+        return fail(c, FSKMC_EINVAL, "nesting is built for the 2D spin-flip models (ADSDES, ISING_ARRHENIUS)");
+    if (inner != FSKMC_LIE && inner != FSKMC_STRANG)
+        return fail(c, FSKMC_EINVAL, "inner schedule must be LIE or STRANG");
+    if (n_inner < 1) return fail(c, FSKMC_EINVAL, "n_inner must be >= 1");
+    if (sup.qx < 2 * c->qx || sup.qy < 2 * c->qy || sup.qx % (2 * c->qx) || sup.qy % (2 * c->qy))
+        return fail(c, FSKMC_EINVAL, "super-cell %dx%d is not a multiple of twice the cell %dx%d", sup.qx,
+                    sup.qy, c->qx, c->qy);
+    for (const Replica &R : c->reps)
+        if (R.lx % (2 * sup.qx) || R.ly % (2 * sup.qy))
+            return fail(c, FSKMC_EINVAL, "lattice %dx%d is not a multiple of twice the super-cell %dx%d",
+                        R.lx, R.ly, sup.qx, sup.qy);
+    if (c->packed && sup.qx % 32)
+        return fail(c, FSKMC_EINVAL, "bit-packed lattices need super-cells a multiple of 32 wide");
+    if (fskmc::nested_smem(c->model, sup.qx, sup.qy, c->qx, c->qy, 1) > 227 * 1024)
+        return fail(c, FSKMC_EINVAL, "super-cell %dx%d does not fit one block's shared memory", sup.qx, sup.qy);
+    c->nest_qx = sup.qx;
+    c->nest_qy = sup.qy;
+    c->nest_inner = (int)inner;
+    c->nest_n = n_inner;
     return FSKMC_OK;
 }
 
@@ -776,10 +860,10 @@ fskmc_status fskmc_run(fskmc_ctx *c, fskmc_scheme scheme, double dt, double T, u
     std::vector<std::vector<Win>> sched(per_replica ? c->nrep : 1);
     for (size_t r = 0; r < sched.size(); ++r)
         build_schedule(scheme, n, dt, seed, c->reps[r].rep, c->w, sched[r]);
-    fskmc_status st = exec_windows(c, sched, seed);
+    fskmc_status st = c->nest_qx ? nested_windows(c, sched, seed) : exec_windows(c, sched, seed);
     if (st) return st;
     c->w += sched[0].size();
-    c->windows += sched[0].size();
+    c->windows += sched[0].size() * (c->nest_qx ? (uint64_t)(c->nest_inner == FSKMC_LIE ? 2 : 3) * c->nest_n : 1);
     return FSKMC_OK;
 }
 
@@ -789,10 +873,10 @@ fskmc_status fskmc_window(fskmc_ctx *c, int32_t colour, double h, uint64_t seed)
     if (colour != 0 && colour != 1) return fail(c, FSKMC_EINVAL, "colour must be 0 or 1");
     if (!(h > 0.0) || !std::isfinite(h)) return fail(c, FSKMC_EINVAL, "window length must be > 0");
     std::vector<std::vector<Win>> sched(1, std::vector<Win>{{colour, h}});
-    fskmc_status st = exec_windows(c, sched, seed);
+    fskmc_status st = c->nest_qx ? nested_windows(c, sched, seed) : exec_windows(c, sched, seed);
     if (st) return st;
     c->w += 1;
-    c->windows += 1;
+    c->windows += c->nest_qx ? (uint64_t)(c->nest_inner == FSKMC_LIE ? 2 : 3) * c->nest_n : 1;
     return FSKMC_OK;
 }
 

@@ -72,6 +72,33 @@ struct WindowArgs {
     int32_t screen;            // binary64 clock: screened window-edge decisions (edge_screen)
 };
 
+// Arguments of one outer window of the nested (two-level) scheme over the
+// super-cells of one colour of one replica (fskmc_nested.cu).
+struct NestedArgs {
+    const Replica *reps;       // device array
+    int32_t rep_index;
+    CellGeom geom;             // sub-cell shape
+    int32_t Qx, Qy;            // super-cell shape (Qx % 2qx == 0, Qy % 2qy == 0)
+    int32_t colour;            // outer colour C: 0 = E, 1 = O
+    uint32_t w0;               // window index of the first inner window (w_outer * ninner)
+    int32_t inner;             // inner schedule: 0 Lie, 1 Strang
+    int32_t ninner;            // inner windows per outer window
+    double d, dhalf;           // inner step h / n_in and its half
+    uint64_t seed;
+    uint8_t *lat;              // all replicas, updated in place
+    int32_t *workload;         // events per sub-cell in its latest inner window
+    unsigned long long *counters;
+    int32_t packed;            // 1 bit per site in device memory (then Qx % 32 == 0)
+    int32_t screen;            // binary64 clock: screened window-edge decisions
+    int32_t super_bytes;       // shared bytes of the staged super-cell (16-byte multiple)
+};
+
+// Shared-memory bytes of one nested block (super-cell + wpb sub-cell warps),
+// and the launch of one outer window (nsuper_active blocks).
+size_t nested_smem(int model, int Qx, int Qy, int qx, int qy, int wpb);
+cudaError_t launch_nested(int model, int fp32, const NestedArgs &a, int nsuper_active, int wpb,
+                          cudaStream_t s);
+
 // Shared-memory bytes one warp of the window kernel needs.
 size_t window_smem_per_warp(int model, int qx, int qy);
 

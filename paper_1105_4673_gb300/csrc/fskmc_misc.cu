@@ -317,9 +317,125 @@ cudaError_t launch_validate(const uint8_t *lat, int64_t n, int nstates, unsigned
     return cudaGetLastError();
 }
 
+// Word-parallel observables for lattices whose rows are whole 32-site words
+// (lx % 32 == 0, rows 16-byte aligned) and r <= 32: the indicator of state
+// 1 is packed 32 sites per word (bit t of word c of row y = site
+// (32c + t, y)), and every sum becomes popcounts of ANDs of words --
+//   pairs   = sum popc(w & (w >> 1 | next << 31)) + popc(w & below)
+//   G_x(r)  = sum popc(w & funnel(w, next, r)),   G_y(r) = sum popc(w & w[y + r])
+// (next: the word to the right, below / w[y + r]: the same column r rows
+// down, both periodic). A block stages the indicator words of OBS_TY rows
+// and OBS_CW word columns, plus r_max rows below and one column to the right,
+// in shared memory; the byte lattice is read once with 16-byte loads
+// (plus r_max / OBS_TY of it again for the rows below). Exact integer sums,
+// equal to the site-by-site kernel's.
+constexpr int OBS_TY = 32, OBS_CW = 32, OBS_RMAX_WORDS = 32;
+
+// Bytes v (4 sites) -> 4 indicator bits of state `st` at bits 0..3, by a
+// bytewise compare and one multiply that gathers the compare's top bits.
+__device__ __forceinline__ uint32_t nibble_eq(uint32_t v, uint32_t st4)
+{
+    const uint32_t t = (__vcmpeq4(v, st4) & 0x80808080u) >> 7;  // bits 0, 8, 16, 24
+    return (t * 0x00204081u) >> 21 & 0xFu;
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(256) observables_words_kernel(const uint8_t *lat, int lx, int ly,
+                                                                 int rmax, unsigned long long *out)
+{
+    __shared__ uint32_t S[(OBS_TY + OBS_RMAX_WORDS) * (OBS_CW + 1)];
+    __shared__ unsigned int acc[4 + 2 * OBS_RMAX_WORDS];
+    const int nacc = 4 + 2 * rmax;
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0;
+    const bool vert = ly > 1;
+    const int nw = lx >> 5;
+    const int c0 = blockIdx.x * OBS_CW, y0 = blockIdx.y * OBS_TY;
+    const int cw = min(OBS_CW, nw - c0), ty = min(OBS_TY, ly - y0);
+    const int rows = ty + (vert ? rmax : 0);
+    const int SW = OBS_CW + 1;
+    // stage the indicator words (rows and columns periodic); count states
+    // 1 and 2 in this tile's own words
+    unsigned int n1 = 0, n2 = 0;
+    for (int i = threadIdx.x; i < rows * (cw + 1); i += blockDim.x) {
+        const int r = i / (cw + 1), c = i - r * (cw + 1);
+        int gy = y0 + r;
+        while (gy >= ly) gy -= ly;
+        int gc = c0 + c;
+        if (gc >= nw) gc -= nw;
+        uint32_t word, w2 = 0u;
+        if (PACKED) {
+            word = reinterpret_cast<const uint32_t *>(lat)[(int64_t)gy * nw + gc];
+        } else {
+            const uint4 *p = reinterpret_cast<const uint4 *>(lat + (int64_t)gy * lx + 32 * gc);
+            const uint4 a = p[0], b = p[1];
+            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+            word = 0u;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                word |= nibble_eq(v[k], 0x01010101u) << (4 * k);
+                w2 |= nibble_eq(v[k], 0x02020202u) << (4 * k);
+            }
+        }
+        S[r * SW + c] = word;
+        if (r < ty && c < cw) {
+            n1 += __popc(word);
+            n2 += __popc(w2);
+        }
+    }
+    __syncthreads();
+    unsigned int pr = 0;
+    unsigned int gx[OBS_RMAX_WORDS], gy[OBS_RMAX_WORDS];
+#pragma unroll
+    for (int r = 0; r < OBS_RMAX_WORDS; ++r) gx[r] = gy[r] = 0u;
+    for (int i = threadIdx.x; i < ty * cw; i += blockDim.x) {
+        const int r = i / cw, c = i - r * cw;
+        const uint32_t w = S[r * SW + c], nx = S[r * SW + c + 1];
+        pr += __popc(w & __funnelshift_r(w, nx, 1));
+        if (vert) pr += __popc(w & S[(r + 1) * SW + c]);
+#pragma unroll
+        for (int d = 1; d <= OBS_RMAX_WORDS; ++d) {
+            if (d > rmax) break;
+            gx[d - 1] += __popc(w & __funnelshift_rc(w, nx, d));
+            if (vert) gy[d - 1] += __popc(w & S[(r + d) * SW + c]);
+        }
+    }
+    // block sums: warp reduce, then shared atomics
+    const int lane = threadIdx.x & 31;
+    const unsigned int ncell = (unsigned int)(ty * cw) * 32u;
+    {
+        const unsigned int a1 = __reduce_add_sync(0xffffffffu, n1);
+        const unsigned int a2 = __reduce_add_sync(0xffffffffu, n2);
+        const unsigned int ap = __reduce_add_sync(0xffffffffu, pr);
+        if (lane == 0) { atomicAdd(&acc[1], a1); atomicAdd(&acc[2], a2); atomicAdd(&acc[3], ap); }
+    }
+#pragma unroll
+    for (int d = 0; d < OBS_RMAX_WORDS; ++d) {
+        if (d >= rmax) break;
+        const unsigned int a = __reduce_add_sync(0xffffffffu, gx[d]);
+        const unsigned int b = __reduce_add_sync(0xffffffffu, gy[d]);
+        if (lane == 0) {
+            if (a) atomicAdd(&acc[4 + d], a);
+            if (b) atomicAdd(&acc[4 + rmax + d], b);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) acc[0] = ncell - acc[1] - acc[2];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nacc; i += blockDim.x)
+        if (acc[i]) atomicAdd(&out[i], (unsigned long long)acc[i]);
+}
+
 cudaError_t launch_observables(const uint8_t *lat, int lx, int ly, int rmax,
                                unsigned long long *out, cudaStream_t s, bool packed)
 {
+    const bool words = (lx & 31) == 0 && rmax <= OBS_RMAX_WORDS &&
+                       (reinterpret_cast<uintptr_t>(lat) & 15u) == 0;
+    if (words) {
+        const dim3 grid((unsigned)((lx / 32 + OBS_CW - 1) / OBS_CW), (unsigned)((ly + OBS_TY - 1) / OBS_TY));
+        if (packed) observables_words_kernel<true><<<grid, 256, 0, s>>>(lat, lx, ly, rmax, out);
+        else observables_words_kernel<false><<<grid, 256, 0, s>>>(lat, lx, ly, rmax, out);
+        return cudaGetLastError();
+    }
     const int64_t tasks = (int64_t)ly * ((lx + OBS_CHUNK - 1) / OBS_CHUNK);
     const int grid = tasks < 152 * 8 ? (int)tasks : 152 * 8;
     size_t smem = sizeof(unsigned int) * (size_t)(4 + 2 * rmax);

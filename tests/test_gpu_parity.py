@@ -177,3 +177,33 @@ def test_flagged_window_takes_the_replay_path():
                          lambda: oracle.FSRun(lx, ly, *q, "ADSDES", rates, init), "LIE", h, h, seed,
                          what=f"flagged window, {engine}")
         assert n <= 1
+
+
+@pytest.mark.parametrize("model,lx,ly,packed", [
+    ("ZGB", 32, 2, False), ("ZGB", 64, 8, False), ("ZGB", 1056, 40, False), ("ISING", 2048, 64, True),
+    ("ADSDES", 96, 34, False), ("ISING1D", 2048, 1, False), ("ISING1D", 4096, 1, True),
+    ("ZGB", 1024, 1024, False),
+])
+@pytest.mark.parametrize("rmax", [0, 1, 7, 32])
+def test_observables_word_path_bit_exact(model, lx, ly, packed, rmax):
+    """The word-parallel observables (rows of whole 32-site words, r <= 32):
+    partial word chunks, lattices shorter than the staged rows, rings, both
+    storages, against the oracle's site-by-site sums."""
+    if rmax > lx or (ly > 1 and rmax > ly):
+        pytest.skip("r beyond the lattice")
+    nstates = 3 if model == "ZGB" else 2
+    lat = random_lattice(lx, ly, nstates, lx + ly + rmax)
+    q = (1, 1) if model != "ZGB" else (2, 2) if ly >= 4 else (2, 1)
+    if model == "ZGB" and ly < 4:
+        model_ctx = "ADSDES"  # a two-row lattice is too short for two-site cells; same sums
+        lat = random_lattice(lx, ly, 2, lx + ly + rmax)
+    else:
+        model_ctx = model
+    with F.Context(lx, ly, model_ctx, RATES.get(model_ctx, dict(ka=1.0, kd=1.0, betaJ=0.5)), q,
+                   bitpacked=packed) as c:
+        c.set_state(lat)
+        cov, en, pc = c.observables(0, rmax)
+    ocov, oen, opc = oracle.observables(lx, ly, model_ctx, lat, rmax)
+    assert np.array_equal(cov, ocov)
+    assert (np.isnan(en) and np.isnan(oen)) or en == oen
+    assert np.array_equal(pc, opc)

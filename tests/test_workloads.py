@@ -6,7 +6,7 @@ recipe -- sides uniform on {64, 128, 256, 512}, betaJ uniform on
 seed."""
 import numpy as np
 
-from workloads import WORKLOADS, ensemble_replicas, sample_shape
+from workloads import WORKLOADS, cpu_sample, ensemble_replicas
 
 
 def test_lattices_admit_the_checkerboard():
@@ -28,8 +28,13 @@ def test_stated_shapes_and_rates():
     assert WORKLOADS["diffusion4096"]["scheme"] == "RANDOM_ORDER"
     assert WORKLOADS["zgb16384"]["scheme"] == "STRANG" and WORKLOADS["zgb16384"]["q"] == (32, 32)
     assert WORKLOADS["ising1d32768"]["ly"] == 1 and WORKLOADS["ising1d32768"]["lx"] == 1 << 15
-    assert sample_shape(WORKLOADS["ising1d32768"]) == (8192, 1)
-    assert sample_shape(WORKLOADS["ising1024"]) == (256, 256)
+    assert cpu_sample(WORKLOADS["ising1d32768"]) == (8192, 1)
+    assert cpu_sample(WORKLOADS["ising1024"]) == (256, 256)
+    # the all-core sample gives every thread at least 16 active cells
+    for name in ("zgb16384", "ising1024", "diffusion4096", "ising1d32768"):
+        w = WORKLOADS[name]
+        lx, ly = cpu_sample(w, 16)
+        assert (lx // w["q"][0]) * (ly // w["q"][1]) // 2 >= 16 * 16, name
 
 
 def test_ensemble_recipe():

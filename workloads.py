@@ -42,10 +42,21 @@ WORKLOADS = {
 }
 
 
-def sample_shape(w: dict) -> tuple[int, int]:
+def cpu_sample(w: dict, threads: int = 1) -> tuple[int, int]:
     """A bounded sample of a workload for the host-CPU oracle timing: a
-    256 x 256 lattice, or a ring of 8192 sites for the 1D model."""
-    return (8192, 1) if w["model"] == "ISING1D" else (256, 256)
+    256 x 256 lattice (a ring of 8192 sites for the 1D model) for one
+    thread; for the all-core form a lattice with at least 16 active cells
+    per thread (up to 2048 x 2048), so that every thread has cells to run."""
+    if w["model"] == "ISING1D":
+        n = 8192
+        while threads > 1 and n // w["q"][0] // 2 < 16 * threads and n < (1 << 20):
+            n *= 2
+        return n, 1
+    side = 256
+    qx, qy = w["q"]
+    while threads > 1 and (side // qx) * (side // qy) // 2 < 16 * threads and side < 2048:
+        side *= 2
+    return side, side
 
 
 def ensemble_replicas(n: int = 512, seed: int = SEED_BASE + 3):
