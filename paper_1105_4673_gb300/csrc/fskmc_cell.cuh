@@ -167,7 +167,8 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     const int lx = at.lx, ly = at.ly;
     const uint32_t m = at.m;
     const int X0 = at.X0, Y0 = at.Y0;
-    const int BW = Lo.BW, BH = Lo.BH, SW = Lo.SW, nsite = Lo.nsite;
+    const int BW = Lo.BW, BH = Lo.BH, nsite = Lo.nsite;
+    constexpr int SW = TR::KB ? 8 : 0;
     const int NL = (nsite + 31) >> 5;  // lanes that own sites
 
     // ZGB with 32-wide cells: rows are staged one per step so that warp
@@ -175,45 +176,40 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
     const bool zrow = (MODEL == ZGB) && !PACKED && qx == 32;
     const bool drow = (MODEL == DIFFUSION) && qx == 32;
     if (drow || zrow) {
-        // UR rows' loads in flight (the row's 32 sites, one per lane, and its
-        // halo sites in a few lanes) before their stores and ballots
-        constexpr int UR = 8;
+        // Every row of the box in flight at once: each row as four aligned
+        // 16-byte chunks -- the 16 sites left of the cell, its 32 sites, the
+        // 16 sites right of it -- copied asynchronously into a staging area
+        // (the membership-mask region, not used yet), then read back one
+        // site per lane for the box and the row ballots.
         // diffusion: halo columns x = -2, -1, 32, 33 in lanes 1..4; ZGB:
         // x = -1 in lane 1, x = 32 in lane 2
         const int hx = drow ? (lane <= 2 ? lane - 3 : 32 + (lane - 3)) : (lane == 1 ? -1 : 32);
         const bool hl = drow ? (lane >= 1 && lane <= 4) : (lane == 1 || lane == 2);
-        int hgx = X0 + hx;
-        hgx += (hgx < 0) ? lx : 0; hgx -= (hgx >= lx) ? lx : 0;
-        for (int by0 = 0; by0 < BH; by0 += UR) {
-            uint32_t v[UR], hv[UR];
-#pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int by = by0 + u;
-                v[u] = 0u;
-                hv[u] = 0u;
-                if (by < BH) {
-                    int gy = Y0 - HW + by;
-                    gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-                    const uint8_t *srow = src + (int64_t)gy * lx;
-                    v[u] = ld_site<PERSIST>(srow + X0 + lane);
-                    if (hl) hv[u] = ld_site<PERSIST>(srow + hgx);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int by = by0 + u;
-                if (by >= BH) break;
-                box[by * BW + HW + lane] = (uint8_t)v[u];
-                if (hl) box[by * BW + HW + hx] = (uint8_t)hv[u];
-                if (drow) {
-                    const uint32_t mo = __ballot_sync(0xffffffffu, v[u] == 1u);
-                    if (lane == 0) rowm[by] = mo;
-                } else {
-                    const uint32_t me = __ballot_sync(0xffffffffu, v[u] == 0u);
-                    const uint32_t ma = __ballot_sync(0xffffffffu, v[u] == 1u);
-                    const uint32_t mb = __ballot_sync(0xffffffffu, v[u] == 2u);
-                    if (lane == 0) { rowm[by] = me; rowm[BH + by] = ma; rowm[2 * BH + by] = mb; }
-                }
+        uint8_t *raw = reinterpret_cast<uint8_t *>(sitemask);
+        const int xl = X0 >= 16 ? X0 - 16 : X0 - 16 + lx;      // the chunk left of the cell
+        const int xr = X0 + 32 < lx ? X0 + 32 : X0 + 32 - lx;  // and the one right of it
+        for (int i = lane; i < 4 * BH; i += 32) {
+            const int by = i >> 2, part = i & 3;
+            int gy = Y0 - HW + by;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            const int gx = part == 0 ? xl : (part == 3 ? xr : X0 + 16 * (part - 1));
+            cp_async16(raw + by * 64 + 16 * part, src + (int64_t)gy * lx + gx);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        for (int by = 0; by < BH; ++by) {
+            const uint8_t *rr = raw + by * 64 + 16;  // rr[x]: site x of the row, -16 <= x < 48
+            const uint32_t v = rr[lane];
+            box[by * BW + HW + lane] = (uint8_t)v;
+            if (hl) box[by * BW + HW + hx] = rr[hx];
+            if (drow) {
+                const uint32_t mo = __ballot_sync(0xffffffffu, v == 1u);
+                if (lane == 0) rowm[by] = mo;
+            } else {
+                const uint32_t me = __ballot_sync(0xffffffffu, v == 0u);
+                const uint32_t ma = __ballot_sync(0xffffffffu, v == 1u);
+                const uint32_t mb = __ballot_sync(0xffffffffu, v == 2u);
+                if (lane == 0) { rowm[by] = me; rowm[BH + by] = ma; rowm[2 * BH + by] = mb; }
             }
         }
     } else {
@@ -454,7 +450,7 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             // exact integer prefix sums over the classes (lanes 0..15)
             P_lane = (uint64_t)(uint32_t)n_lane * rq_lane;
 #pragma unroll
-            for (int off = 1; off < 16; off <<= 1) {
+            for (int off = 1; off < K; off <<= 1) {
                 uint64_t v = __shfl_up_sync(0xffffffffu, P_lane, off);
                 if (lane >= off) P_lane += v;
             }
@@ -569,7 +565,8 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
             c = __popc(sitemask[mk * 32 + lane]);
         }
         int incl = c;
-        for (int off = 1; off < NL; off <<= 1) {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
             int v = __shfl_up_sync(0xffffffffu, incl, off);
             if (lane >= off) incl += v;
         }

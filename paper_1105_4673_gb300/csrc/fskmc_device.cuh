@@ -352,6 +352,20 @@ __device__ __forceinline__ double neg_log_u53(uint64_t n)
 
 // Global-memory access for staging: through L2 only in the persistent
 // kernel, whose cells read sites that other SMs wrote within the same launch.
+// Asynchronous 16-byte copy global -> shared (cp.async, cached in L2 only,
+// so data other SMs wrote before an acquire are seen), and the wait for all
+// of this thread's copies in flight. Both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 template <bool PERSIST>
 __device__ __forceinline__ uint8_t ld_site(const uint8_t *p)
 {

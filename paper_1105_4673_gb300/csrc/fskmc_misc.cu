@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256) observables_words_kernel(const uint8_t *l
     const int nw = lx >> 5;
     const int c0 = blockIdx.x * OBS_CW, y0 = blockIdx.y * OBS_TY;
     const int cw = min(OBS_CW, nw - c0), ty = min(OBS_TY, ly - y0);
-    const int rows = ty + (vert ? rmax : 0);
+    const int rows = ty + (vert ? max(rmax, 1) : 0);  // the rows below: G_y and the vertical pairs
     const int SW = OBS_CW + 1;
     // stage the indicator words (rows and columns periodic); count states
     // 1 and 2 in this tile's own words
