@@ -817,6 +817,25 @@ __device__ uint32_t cell_window(uint8_t *wsm, const Replica &R, const CellGeom &
                 atomicOr(drow + wi, bits);
             }
         }
+    } else if (zrow) {
+        // 32-wide ZGB cells: lane L writes row L in two 16-byte stores, its
+        // bytes rebuilt from the row's own-site class masks (empty = class 0,
+        // A = class 3, B = neither), which the events keep current
+        if (lane < qy) {
+            const uint32_t am = sitemask[mask_of<MODEL>(3) * 32 + lane];
+            const uint32_t bm = ~(sitemask[mask_of<MODEL>(0) * 32 + lane] | am);
+            uint32_t wv[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                // 4 mask bits -> 4 bytes of 0/1 (bit k to bit 8k by one multiply)
+                const uint32_t ea = (((am >> (4 * g)) & 0xFu) * 0x00204081u) & 0x01010101u;
+                const uint32_t eb = (((bm >> (4 * g)) & 0xFu) * 0x00204081u) & 0x01010101u;
+                wv[g] = ea + 2u * eb;
+            }
+            uint4 *d = reinterpret_cast<uint4 *>(dst + (int64_t)(Y0 + lane) * lx + X0);
+            d[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            d[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+        }
     } else {
         for (int i = lane; i < nsite; i += 32) {
             int lly = (int)fdiv((uint32_t)i, G.fqx), llx = i - lly * qx;
