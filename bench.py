@@ -70,11 +70,17 @@ def parse():
                    help="several small spin-flip cells per warp (on), one cell per warp (off), "
                         "or the library's choice (auto)")
     p.add_argument("--clock", default="fp32", choices=["fp64", "fp32"], help="ensemble512 only")
-    p.add_argument("--study", default=None, choices=["weak-order", "weak-order-replicas", "clock-error"],
+    p.add_argument("--study", default=None,
+                   choices=["weak-order", "weak-order-replicas", "clock-error", "nested"],
                    help="instead of the throughput line: the weak-order study of the 1024^2 Ising "
                         "workload (Lie and Strang, dt in {1, 1/2, 1/4, 1/8} against the dt -> 0 "
                         "limit), or the binary32-vs-binary64 clock error of the workload's observables")
     p.add_argument("--betaJ", type=float, default=None, help="weak-order study: coupling (default: the workload's)")
+    p.add_argument("--dts", default="1,0.5,0.25,0.125", help="weak-order studies: the window lengths")
+    p.add_argument("--ref-dt", type=float, default=1.0 / 32, help="weak-order studies: the reference window")
+    p.add_argument("--study-T", type=float, default=1.0, help="weak-order-replicas: physical time")
+    p.add_argument("--replicas", type=int, default=8192, help="weak-order-replicas: replicas per batch")
+    p.add_argument("--batches", type=int, default=4, help="weak-order-replicas: batches per point")
     return p.parse_args()
 
 
@@ -181,8 +187,10 @@ def algo_lane_ops_per_event(model, q, fp64):
 # workload and the issue-slot utilisation.
 PROFILED = {
     ("fs_persistent_kernel<ZGB,float>", "zgb16384"): {
-        "src": ["fskmc_window.cu", "fskmc_device.cuh"], "dram_bytes_per_window": None,
-        "issue_active": None, "src_sha256": None},
+        "src": ["fskmc_window.cu", "fskmc_cell.cuh", "fskmc_device.cuh", "fskmc_internal.h",
+                "fskmc_persistent.h"],
+        "dram_bytes_per_window": 498310433, "issue_active": 0.773,
+        "src_sha256": "c9f00f4fa26a6350525a1e63af1d58b31dd6f6773a2ba9e2d494da2c3920372c"},
 }
 
 
@@ -589,6 +597,7 @@ def run_ensemble(args, rank, world, local):
     b.set_warps_per_block(wpb)
     b.set_clock(clock)
     b.set_cell_grouping({"auto": "AUTO", "on": True, "off": False}[args.grouping])
+    b.set_task_order(args.order.upper())
     b.init_random(seed, w["coverage"])
     step_t = STEP_WINDOWS_DT * w["dt"]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -650,7 +659,7 @@ def run_ensemble(args, rank, world, local):
                                f"U[0.2,0.8], ka/kd logU[0.1,10], {w['scheme']} dt={w['dt']}",
                    "step": f"{step_t:g} time units for every replica, one persistent launch",
                    "clock": args.clock, "engine": "persistent", "cell": f"{q[0]}x{q[1]}" + ("" if args.cell else " (autotuned)"),
-                   "warps_per_cta": wpb, "lanes_per_cell": lanes, "sites": nbytes,
+                   "warps_per_cta": wpb, "lanes_per_cell": lanes, "sites": nbytes, "task_order": args.order,
                    "cells": cells, "l2": "flushed between timed steps"},
         "comparison": {"one_replica_at_a_time_plain_fp64": one_at_a_time},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_G,
@@ -771,22 +780,23 @@ def study_weak_order(args):
     print(json.dumps(out), flush=True)
 
 
-def study_weak_order_replicas(args, L=32, q=2, M=8192, batches=4, T=1.0):
+def study_weak_order_replicas(args, L=32, q=2):
     """Weak-error order resolved on many small replicas (cells of 2 x 2 sites
-    put every site on a cell edge, where the splitting error lives): M
-    replicas of an L x L Ising lattice, advanced to time T in one persistent binary64 launch per batch;
-    the replica mean of the energy, coverage and G(1) at T (each batch's
-    replicas start from their own Bernoulli(1/2) draw, the same draws in
-    every arm) for Lie and
-    Strang at dt in {1, 1/2, 1/4, 1/8} against Strang at dt = 1/32, and the
-    order fitted over the points resolved beyond 3 standard errors."""
+    put every site on a cell edge, where the splitting error lives): batches
+    of M replicas of an L x L Ising lattice, each batch advanced to time T
+    in one persistent binary64 launch, every replica from its own
+    Bernoulli(1/2) draw (the same draws in every arm); the replica mean of
+    the energy, coverage and G(1) at T for Lie and Strang at the given
+    window lengths against Strang at a much shorter one, and the order
+    fitted over the points resolved beyond 3 standard errors."""
     import torch
 
     import paper_1105_4673_gb300 as F
     stream = torch.cuda.current_stream()
     betaJ = 0.6 if args.betaJ is None else args.betaJ
     rates = dict(ka=1.0, kd=1.0, betaJ=betaJ)
-    dts = [1.0, 0.5, 0.25, 0.125]
+    dts = [float(x) for x in args.dts.split(",")]
+    M, batches, T = args.replicas, args.batches, args.study_T
 
     def arm(scheme, dt):
         vals = []
@@ -804,10 +814,11 @@ def study_weak_order_replicas(args, L=32, q=2, M=8192, batches=4, T=1.0):
         return a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(len(a))
 
     t0 = time.time()
-    ref_m, ref_s = arm("STRANG", 1.0 / 32)
+    ref_m, ref_s = arm("STRANG", args.ref_dt)
     names = ["energy", "coverage", "Gx(1)"]
     out = {"workload": f"{M * batches} replicas of {L}x{L} ISING betaJ={betaJ}, {q}x{q} cells, T={T}, "
-                       "from Bernoulli(1/2) states", "reference": "Strang at dt = 1/32", "schemes": {}}
+                       "from Bernoulli(1/2) states", "reference": f"Strang at dt = {args.ref_dt:g}",
+           "schemes": {}}
     for scheme in ("LIE", "STRANG"):
         rows = [arm(scheme, dt) for dt in dts]
         per = {}
@@ -821,6 +832,44 @@ def study_weak_order_replicas(args, L=32, q=2, M=8192, batches=4, T=1.0):
                       "order": None if fit is None else fit[0], "order_se": None if fit is None else fit[1]}
         out["schemes"][scheme] = {"dt": dts, "observables": per}
     out["seconds"] = time.time() - t0
+    print(json.dumps(out), flush=True)
+
+
+def study_nested(args, L=4096, steps=4):
+    """The nested two-level scheme (Section 5) beside the one-level scheme on
+    the same lattice: a 4096^2 Ising lattice (betaJ = 0.4407, Lie dt = 1),
+    one-level with 16x16 cells (the grouped kernels) and nested with 64x64
+    super-cells of 16x16 sub-cells (n_in inner Lie steps per outer window),
+    both clocks; events/s over `steps` runs of 10 dt after 3 warm-up runs."""
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    stream = torch.cuda.current_stream()
+    rates = dict(ka=1.0, kd=1.0, betaJ=0.4407)
+    out = {"lattice": f"{L}x{L} ISING betaJ=0.4407, Lie dt=1", "forms": {}}
+    forms = [("one-level 16x16 cells", None, 1)] + [(f"nested 64x64 / 16x16, n_in={n}", (64, 64), n)
+                                                    for n in (1, 2, 4)]
+    for name, sup, n_in in forms:
+        for clock in ("FP64", "FP32"):
+            c = F.Context(L, L, "ISING", rates, (16, 16), stream=stream)
+            c.set_clock(clock)
+            if sup:
+                c.set_nesting(sup, "LIE", n_in)
+            c.init_random(99, 0.5)
+            for _ in range(3):
+                c.run("LIE", 1.0, 10.0, 99)
+            torch.cuda.synchronize()
+            e0 = c.stats()["events"]
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                c.run("LIE", 1.0, 10.0, 99)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ev = c.stats()["events"] - e0
+            out["forms"][f"{name} {clock}"] = {"events_per_s": ev / (a.elapsed_time(b) / 1000.0),
+                                              "events": ev, "ms": a.elapsed_time(b)}
+            c.close()
     print(json.dumps(out), flush=True)
 
 
@@ -893,6 +942,9 @@ def main():
         return
     if args.study == "weak-order-replicas":
         study_weak_order_replicas(args)
+        return
+    if args.study == "nested":
+        study_nested(args)
         return
     if args.study == "clock-error":
         study_clock_error(args)
