@@ -71,7 +71,7 @@ def parse():
                         "or the library's choice (auto)")
     p.add_argument("--clock", default="fp32", choices=["fp64", "fp32"], help="ensemble512 only")
     p.add_argument("--study", default=None,
-                   choices=["weak-order", "weak-order-replicas", "clock-error", "nested"],
+                   choices=["weak-order", "weak-order-replicas", "clock-error", "nested", "dt-error-scaling"],
                    help="instead of the throughput line: the weak-order study of the 1024^2 Ising "
                         "workload (Lie and Strang, dt in {1, 1/2, 1/4, 1/8} against the dt -> 0 "
                         "limit), or the binary32-vs-binary64 clock error of the workload's observables")
@@ -873,6 +873,56 @@ def study_nested(args, L=4096, steps=4):
     print(json.dumps(out), flush=True)
 
 
+def study_dt_error_scaling(args):
+    """The workload's dt-error at larger windows, where it is resolved, and
+    its order: the binary64 form at dt in {16, 8, 4, 2, 1} x the workload's
+    dt against dt/4 of the workload, each over independent runs to time
+    --dt-error-T from the initial state; the weighted fit e = C dt^p over the
+    resolved points gives the error expected at the workload's own dt (with
+    its standard error from the fit)."""
+    import torch
+
+    import paper_1105_4673_gb300 as F
+    stream = torch.cuda.current_stream()
+    w = WORKLOADS[args.workload]
+    runs, T = max(2, args.dt_error_runs), args.dt_error_T
+    mults = [16, 8, 4, 2, 1]
+
+    def arm(dt):
+        vals = []
+        for s in range(runs):
+            c = make_ctx(F, w, "plain_fp64", stream, w["seed"] + 1000 + s, args)
+            c.run(w["scheme"], dt, T, w["seed"] + 1000 + s)
+            names, v = observable_vector(c, w["model"])
+            vals.append(v)
+            c.close()
+        a = np.array(vals)
+        return names, a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(runs)
+
+    t0 = time.time()
+    names, ref_m, ref_s = arm(w["dt"] / 4)
+    rows = {m: arm(w["dt"] * m)[1:] for m in mults}
+    out = {"workload": args.workload, "T": T, "runs_per_point": runs,
+           "reference": f"binary64 form at dt/4 = {w['dt'] / 4:g}", "dts": [w["dt"] * m for m in mults],
+           "observables": {}}
+    for i, n in enumerate(names):
+        e = [float(rows[m][0][i] - ref_m[i]) for m in mults]
+        se = [float(np.hypot(rows[m][1][i], ref_s[i])) for m in mults]
+        ok = [j for j in range(len(mults)) if abs(e[j]) > 3 * se[j]]
+        entry = {"error": e, "se": se, "resolved_dts": [w["dt"] * mults[j] for j in ok]}
+        if len(ok) >= 2 and len({np.sign(e[j]) for j in ok}) == 1:
+            p_, sp = fit_order([w["dt"] * mults[j] for j in ok], [e[j] for j in ok], [se[j] for j in ok])
+            # C from the largest resolved point, the error at the workload's dt
+            j0 = ok[0]
+            C = e[j0] / (w["dt"] * mults[j0]) ** p_
+            pred = C * w["dt"] ** p_
+            entry.update(order=p_, order_se=sp, predicted_error_at_dt=float(pred),
+                         predicted_rel_se=float(np.hypot(se[j0] / abs(e[j0]), sp * np.log(mults[j0]))))
+        out["observables"][n] = entry
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out), flush=True)
+
+
 def study_clock_error(args):
     """Binary32 minus binary64 window clock, per observable, on the
     workload's own lattice and schedule: several independent runs of each
@@ -942,6 +992,9 @@ def main():
         return
     if args.study == "weak-order-replicas":
         study_weak_order_replicas(args)
+        return
+    if args.study == "dt-error-scaling":
+        study_dt_error_scaling(args)
         return
     if args.study == "nested":
         study_nested(args)

@@ -81,6 +81,9 @@ def lib():
         L.orc_ssa_run.argtypes = [C.c_int, C.c_int, C.c_int, f64p, C.c_double, C.c_uint64,
                                   C.c_uint32, u8p]
         L.orc_ssa_run.restype = C.c_int64
+        L.orc_ssa_bkl_run.argtypes = [C.c_int, C.c_int, C.c_int, f64p, C.c_double, C.c_uint64,
+                                      C.c_uint32, u8p]
+        L.orc_ssa_bkl_run.restype = C.c_int64
         L.orc_total_rate.argtypes = [C.c_int, C.c_int, C.c_int, f64p, u8p, i64p]
         L.orc_total_rate.restype = C.c_double
         L.orc_cell_members.argtypes = [C.c_int] * 5 + [f64p, u8p, C.c_int, C.c_int,
@@ -286,6 +289,15 @@ def ssa_run(lx, ly, model, rates: dict, lattice, T: float, seed: int, replica: i
     """Serial SSA over the whole lattice; returns (lattice, events)."""
     lat = np.ascontiguousarray(lattice, dtype=np.uint8).reshape(-1).copy()
     n = lib().orc_ssa_run(lx, ly, _model(model), _rates6(rates), T, seed, replica, lat)
+    if n < 0:
+        raise ValueError("oracle rejected the SSA arguments")
+    return lat, int(n)
+
+
+def ssa_bkl_run(lx, ly, model, rates: dict, lattice, T: float, seed: int, replica: int = 0):
+    """Serial SSA with class lists (the BKL form); returns (lattice, events)."""
+    lat = np.ascontiguousarray(lattice, dtype=np.uint8).reshape(-1).copy()
+    n = lib().orc_ssa_bkl_run(lx, ly, _model(model), _rates6(rates), T, seed, replica, lat)
     if n < 0:
         raise ValueError("oracle rejected the SSA arguments")
     return lat, int(n)

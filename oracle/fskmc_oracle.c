@@ -22,6 +22,8 @@
  *   orc_fs_run       exact Lie / Strang / random operator products on 4x4
  *                    lattices (chi-square); the J=0 closed form; Onsager
  *   orc_ssa_run      exact e^{TQ} on 3x3 (chi-square); the J=0 closed form
+ *   orc_ssa_bkl_run  exact e^{TQ} on 3x3 (chi-square); observables equal to
+ *                    orc_ssa_run's over replicas (the class-list form)
  *   orc_observables  brute-force recount in numpy
  *   orc_fs_run_threads  equal, lattice for lattice, to orc_fs_run (the cells
  *                    of one colour are independent, Eq. exact)
@@ -740,6 +742,134 @@ int64_t orc_ssa_run(int lx, int ly, int model, const double *rates7, double T,
     }
     free(mb);
     free(stamp);
+    return (int64_t)e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Serial SSA with class lists (the BKL form, Section 1's reference to      */
+/* Bortz-Kalos-Lebowitz): the same classes, rates, draws and time steps as  */
+/* orc_ssa_run, but each class keeps an array of its members, updated by    */
+/* swap-remove when an event changes a member's class, so an event costs    */
+/* O(1) instead of a recount of the lattice. The j-th member of class k is  */
+/* the j-th entry of the class's array (an order of its own), so the        */
+/* trajectory differs from the direct form's while the law is the same;    */
+/* tests cross-check the two (and both against e^{TQ}). Member ids: site i  */
+/* is i, the directed slot from site i in direction d is N + 4i + d.        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t *list;  /* nclass lists of capacity M each */
+    int32_t *cnt;   /* members per class */
+    int32_t *cls;   /* class of each member (-1: none) */
+    int32_t *pos;   /* position of each member in its class's list */
+    int M;
+} bkl_t;
+
+static void bkl_set(bkl_t *B, int m, int k)
+{
+    int k0 = B->cls[m];
+    if (k0 == k) return;
+    if (k0 >= 0) { /* swap-remove from the old list */
+        int p = B->pos[m], last = B->list[(size_t)k0 * B->M + B->cnt[k0] - 1];
+        B->list[(size_t)k0 * B->M + p] = last;
+        B->pos[last] = p;
+        B->cnt[k0]--;
+    }
+    if (k >= 0) {
+        B->list[(size_t)k * B->M + B->cnt[k]] = m;
+        B->pos[m] = B->cnt[k]++;
+    }
+    B->cls[m] = k;
+}
+
+/* the class of member m on the whole lattice */
+static int bkl_class(const view_t *v, int m)
+{
+    const sys_t *S = v->S;
+    int N = S->lx * S->ly;
+    if (m < N) return site_class(v, m % S->lx, m / S->lx);
+    int i = (m - N) >> 2, d = (m - N) & 3;
+    int x = i % S->lx, y = i / S->lx;
+    return slot_class(v, x, y, x + DX[d], y + DY[d]);
+}
+
+/* re-class every member whose class can depend on site c: the sites within
+ * one step of c and the slots leaving them (a class depends on the states
+ * of its site or slot ends and, for the n-dependent rates, on the states of
+ * the origin's neighbours) */
+static void bkl_touch(bkl_t *B, const view_t *v, int c)
+{
+    const sys_t *S = v->S;
+    int N = S->lx * S->ly, cx = c % S->lx, cy = c / S->lx;
+    for (int k = -1; k < 4; k++) {
+        int x = k < 0 ? cx : cx + DX[k], y = k < 0 ? cy : cy + DY[k];
+        if (S->model == ORC_ISING1D && y != cy) continue;
+        int i = sidx(S, x, y);
+        bkl_set(B, i, bkl_class(v, i));
+        if (S->slots)
+            for (int d = 0; d < 4; d++) bkl_set(B, N + 4 * i + d, bkl_class(v, N + 4 * i + d));
+    }
+}
+
+int64_t orc_ssa_bkl_run(int lx, int ly, int model, const double *rates7, double T,
+                        uint64_t seed, uint32_t rep, uint8_t *lat)
+{
+    sys_t S;
+    if (sys_init(&S, lx, ly, lx, ly, model, rates7)) return -1;
+    int N = lx * ly, M = S.slots ? 5 * N : N;
+    bkl_t B;
+    B.M = M;
+    B.list = (int32_t *)malloc(sizeof(int32_t) * (size_t)M * (size_t)S.nclass);
+    B.cnt = (int32_t *)calloc(16, sizeof(int32_t));
+    B.cls = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+    B.pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+    uint32_t *stamp = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    if (!B.list || !B.cnt || !B.cls || !B.pos || !stamp) {
+        free(B.list); free(B.cnt); free(B.cls); free(B.pos); free(stamp);
+        return -1;
+    }
+    for (int i = 0; i < N; i++) stamp[i] = 1; /* the whole lattice is writable */
+    view_t v = {&S, lat, lat, stamp, 1};
+    for (int m = 0; m < M; m++) B.cls[m] = -1;
+    for (int m = 0; m < M; m++) {
+        if (model == ORC_ISING1D && m >= N) break;
+        bkl_set(&B, m, bkl_class(&v, m));
+    }
+    double tau = 0.0;
+    uint64_t e = 0;
+    for (;;) {
+        double lam = 0.0;
+        for (int k = 0; k < S.nclass; k++) lam = fma((double)B.cnt[k], S.r[k], lam);
+        if (lam == 0.0) break;
+        uint32_t o[4];
+        draw(seed, (uint32_t)e, (uint32_t)(e >> 32), 0, rep | (TAG_SSA << 24), o);
+        uint64_t b53 = ((uint64_t)o[0] << 21) | (uint64_t)(o[1] >> 11);
+        double ut = (double)(b53 + 1) * 0x1p-53;
+        double end = tau + (-log(ut) / lam);
+        if (end >= T) break;
+        tau = end;
+        double t = (((double)o[2] + 0.5) * 0x1p-32) * lam;
+        double P = 0.0;
+        int k;
+        for (k = 0; k < S.nclass; k++) {
+            P = fma((double)B.cnt[k], S.r[k], P);
+            if (t < P) break;
+        }
+        uint32_t j = (uint32_t)(((uint64_t)o[3] * (uint64_t)B.cnt[k]) >> 32);
+        int m = B.list[(size_t)k * M + j];
+        member_t mb;
+        if (m < N) {
+            mb.kind = 0; mb.ox = mb.tx = m % lx; mb.oy = mb.ty = m / lx;
+        } else {
+            int i = (m - N) >> 2, d = (m - N) & 3;
+            mb.kind = 1; mb.ox = i % lx; mb.oy = i / lx; mb.tx = mb.ox + DX[d]; mb.ty = mb.oy + DY[d];
+        }
+        mb.cls = k;
+        apply_member(&v, &mb, k);
+        bkl_touch(&B, &v, sidx(&S, mb.ox, mb.oy));
+        if (mb.kind == 1) bkl_touch(&B, &v, sidx(&S, mb.tx, mb.ty));
+        e++;
+    }
+    free(B.list); free(B.cnt); free(B.cls); free(B.pos); free(stamp);
     return (int64_t)e;
 }
 

@@ -34,9 +34,10 @@ def _lib():
     build.build()
 
 
-def _gpu(model, lx, ly, Q, q, packed, init, inner, n_in, clock="FP64"):
+def _gpu(model, lx, ly, Q, q, packed, init, inner, n_in, clock="FP64", grouped=True):
     c = F.Context(lx, ly, model, RATES[model], q, bitpacked=packed)
     c.set_clock(clock)
+    c.set_cell_grouping(grouped)
     c.set_nesting(Q, inner, n_in)
     c.set_state(init)
     return c
@@ -45,12 +46,14 @@ def _gpu(model, lx, ly, Q, q, packed, init, inner, n_in, clock="FP64"):
 @pytest.mark.parametrize("model,lx,ly,Q,q,packed", GEOMS)
 @pytest.mark.parametrize("scheme,inner,n_in", [("LIE", "LIE", 1), ("STRANG", "STRANG", 2),
                                                ("RANDOM", "LIE", 3), ("LIE", "STRANG", 1)])
-def test_nested_bit_exact(model, lx, ly, Q, q, packed, scheme, inner, n_in):
+@pytest.mark.parametrize("grouped", [True, False])  # sub-cells several per warp, or one per warp
+def test_nested_bit_exact(model, lx, ly, Q, q, packed, scheme, inner, n_in, grouped):
     seed = 0x2E57 + lx + ly + n_in
     init = oracle.init_bernoulli(lx, ly, seed, 0.5)
     dt, T = 0.2, 1.0
     orc = oracle.FS2Run(lx, ly, Q, q, model, RATES[model], init).run(scheme, dt, T, seed, inner, n_in)
-    with _gpu(model, lx, ly, Q, q, packed, init, inner, n_in) as c:
+    with _gpu(model, lx, ly, Q, q, packed, init, inner, n_in, grouped=grouped) as c:
+        assert c.info()["lanes_per_cell"] == (8 if grouped else 32)
         c.run(scheme, dt, T, seed)
         st = c.stats()
         g, wl = c.get_state(), c.workload()
