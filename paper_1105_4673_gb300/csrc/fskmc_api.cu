@@ -547,11 +547,12 @@ fskmc_status exec_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &sch
 
 // Warps per block of the nested kernel: one per active sub-cell of a
 // super-cell's inner window, at most 16, fewer if shared memory runs out.
-int nested_wpb(const fskmc_ctx *c)
+int nested_wpb(const fskmc_ctx *c, int lanes)
 {
     const int nact = (c->nest_qx / c->qx) * (c->nest_qy / c->qy) / 2;
-    int wpb = std::min(nact, 16);
-    while (wpb > 1 && fskmc::nested_smem(c->model, c->nest_qx, c->nest_qy, c->qx, c->qy, wpb) > 227 * 1024)
+    const int per_warp = lanes < 32 ? 32 / lanes : 1;
+    int wpb = std::min((nact + per_warp - 1) / per_warp, 16);
+    while (wpb > 1 && fskmc::nested_smem(c->model, c->nest_qx, c->nest_qy, c->qx, c->qy, wpb, lanes) > 227 * 1024)
         --wpb;
     return wpb;
 }
@@ -565,7 +566,8 @@ fskmc_status nested_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &s
     const uint64_t ninner = (uint64_t)(c->nest_inner == FSKMC_LIE ? 2 : 3) * (uint64_t)c->nest_n;
     if ((c->w + nw) * ninner > 0xFFFFFFFFull)
         return fail(c, FSKMC_EINVAL, "nested run: inner window index beyond 2^32");
-    const int wpb = nested_wpb(c);
+    const int lanes = lanes_per_cell(c);
+    const int wpb = nested_wpb(c, lanes);
     const int super_bytes = ((c->nest_qx + 2) * (c->nest_qy + 2) + 15) & ~15;
     for (size_t i = 0; i < nw; ++i) {
         for (int r = 0; r < c->nrep; ++r) {
@@ -590,6 +592,7 @@ fskmc_status nested_windows(fskmc_ctx *c, const std::vector<std::vector<Win>> &s
             a.packed = c->packed ? 1 : 0;
             a.screen = c->edge_screen;
             a.super_bytes = super_bytes;
+            a.lanes = lanes;
             const int nsuper = (R.lx / c->nest_qx) * (R.ly / c->nest_qy) / 2;
             CK(c, fskmc::launch_nested(c->model, c->clock == FSKMC_CLOCK_FP32, a, nsuper, wpb, c->stream));
         }
@@ -729,7 +732,8 @@ fskmc_status fskmc_set_nesting(fskmc_ctx *c, fskmc_cell_shape sup, fskmc_scheme 
                         R.lx, R.ly, sup.qx, sup.qy);
     if (c->packed && sup.qx % 32)
         return fail(c, FSKMC_EINVAL, "bit-packed lattices need super-cells a multiple of 32 wide");
-    if (fskmc::nested_smem(c->model, sup.qx, sup.qy, c->qx, c->qy, 1) > 227 * 1024)
+    if (fskmc::nested_smem(c->model, sup.qx, sup.qy, c->qx, c->qy, 1, 32) > 227 * 1024 ||
+        fskmc::nested_smem(c->model, sup.qx, sup.qy, c->qx, c->qy, 1, fskmc::group_width(c->model, c->qx, c->qy)) > 227 * 1024)
         return fail(c, FSKMC_EINVAL, "super-cell %dx%d does not fit one block's shared memory", sup.qx, sup.qy);
     c->nest_qx = sup.qx;
     c->nest_qy = sup.qy;

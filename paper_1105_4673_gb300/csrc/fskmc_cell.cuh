@@ -20,19 +20,6 @@ namespace fskmc {
 
 namespace {
 
-// Where a cell sits: its origin (X0, Y0) in the periodic lx x ly lattice it
-// is staged from and written back to, and its id m in the random counters
-// (the cell's index in its lattice's cell grid).
-struct CellAt {
-    int X0, Y0, lx, ly;
-    uint32_t m;
-};
-
-__device__ __forceinline__ CellAt cell_at(const Replica &R, const CellGeom &G, int cx, int cy)
-{
-    return CellAt{cx * G.qx, cy * G.qy, R.lx, R.ly, (uint32_t)(cy * R.ncx + cx)};
-}
-
 struct Layout {
     int BW, BH, nsite, s, SW;
     int box_bytes, scls_bytes, sitemask_words, slotmask_words, rowmask_words;

@@ -352,6 +352,19 @@ __device__ __forceinline__ double neg_log_u53(uint64_t n)
 
 // Global-memory access for staging: through L2 only in the persistent
 // kernel, whose cells read sites that other SMs wrote within the same launch.
+// Where a cell sits: its origin (X0, Y0) in the periodic lx x ly lattice it
+// is staged from and written back to, and its id m in the random counters
+// (the cell's index in its lattice's cell grid).
+struct CellAt {
+    int X0, Y0, lx, ly;
+    uint32_t m;
+};
+
+__device__ __forceinline__ CellAt cell_at(const Replica &R, const CellGeom &G, int cx, int cy)
+{
+    return CellAt{cx * G.qx, cy * G.qy, R.lx, R.ly, (uint32_t)(cy * R.ncx + cx)};
+}
+
 // Asynchronous 16-byte copy global -> shared (cp.async, cached in L2 only,
 // so data other SMs wrote before an acquire are seen), and the wait for all
 // of this thread's copies in flight. Both addresses 16-byte aligned.

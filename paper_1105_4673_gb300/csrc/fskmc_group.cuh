@@ -79,7 +79,7 @@ __host__ __device__ inline GLayout make_glayout(int qx, int qy, int W)
 // runs), and owns membership word l for the rank search.
 template <int MODEL, typename CLK, bool PERSIST, bool PACKED, int W>
 __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, const CellGeom &G,
-                             bool valid, int cx, int cy, uint32_t w, double hwin, bool screen, uint64_t seed,
+                             bool valid, const CellAt &at, uint32_t w, double hwin, bool screen, uint64_t seed,
                              const uint8_t *src, uint8_t *dst, int lane, uint32_t *ev_out,
                              bool *amb_out, bool *bad_out, uint32_t *nexact_out)
 {
@@ -103,13 +103,13 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     int *cnt = reinterpret_cast<int *>(csm + Lo.cnt_off);
     double *dcnt = reinterpret_cast<double *>(csm + Lo.dcnt_off);
 
-    const int lx = R.lx, ly = R.ly;
-    const int m = cy * R.ncx + cx;
-    const int X0 = cx * qx, Y0 = cy * qy;
+    const int lx = at.lx, ly = at.ly;
+    const uint32_t m = at.m;
+    const int X0 = at.X0, Y0 = at.Y0;
 
     // Stage the cell and its halo (periodic wrap) from the window-start
     // state; on the ring only the cell's own row.
-    const bool rows16 = !PACKED && (qx & 15) == 0 && (lx & 15) == 0;
+    const bool rows16 = !PACKED && (qx & 15) == 0 && (lx & 15) == 0 && (X0 & 15) == 0;
     if (valid && rows16) {
         // byte lattice, cell width a multiple of 16: each box row is qx/16
         // aligned 16-byte chunks of the cell's row plus its two halo sites;
@@ -622,7 +622,8 @@ __global__ void __launch_bounds__(256) fs_group_kernel(WindowArgs a, int nactive
     uint32_t ev;
     uint32_t nexact;
     bool amb, bad;
-    group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cx, cy, a.w, a.h, a.screen != 0, a.seed,
+    group_window<MODEL, CLK, false, PACKED, W>(csm, Lo, R, a.geom, valid, cell_at(R, a.geom, cx, cy), a.w, a.h,
+                                                a.screen != 0, a.seed,
                                                 a.src + R.lat_off, a.dst + R.lat_off, lane, &ev,
                                                 &amb, &bad, &nexact);
     if (valid && (lane & (W - 1)) == 0) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)ev;
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
         uint32_t ev;
         uint32_t nexact;
         bool amb, bad;
-        group_window<MODEL, CLK, true, PACKED, W>(csm, Lo, R, P.geom, valid, cx, cy, P.w0 + (uint32_t)i,
+        group_window<MODEL, CLK, true, PACKED, W>(csm, Lo, R, P.geom, valid, cell_at(R, P.geom, cx, cy), P.w0 + (uint32_t)i,
                                                    P.h[i], P.screen != 0, P.seed, cur, cur, lane, &ev, &amb, &bad,
                                                    &nexact);
         if (valid && gl == 0) P.workload[R.cell_off + m] = (int32_t)ev;

@@ -91,11 +91,12 @@ struct NestedArgs {
     int32_t packed;            // 1 bit per site in device memory (then Qx % 32 == 0)
     int32_t screen;            // binary64 clock: screened window-edge decisions
     int32_t super_bytes;       // shared bytes of the staged super-cell (16-byte multiple)
+    int32_t lanes;             // lanes per sub-cell: 32 (one per warp) or 8 / 16 (grouped)
 };
 
 // Shared-memory bytes of one nested block (super-cell + wpb sub-cell warps),
 // and the launch of one outer window (nsuper_active blocks).
-size_t nested_smem(int model, int Qx, int Qy, int qx, int qy, int wpb);
+size_t nested_smem(int model, int Qx, int Qy, int qx, int qy, int wpb, int lanes);
 cudaError_t launch_nested(int model, int fp32, const NestedArgs &a, int nsuper_active, int wpb,
                           cudaStream_t s);
 
