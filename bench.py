@@ -190,7 +190,7 @@ PROFILED = {
         "src": ["fskmc_window.cu", "fskmc_cell.cuh", "fskmc_device.cuh", "fskmc_internal.h",
                 "fskmc_persistent.h"],
         "dram_bytes_per_window": 498310433, "issue_active": 0.773,
-        "src_sha256": "c9f00f4fa26a6350525a1e63af1d58b31dd6f6773a2ba9e2d494da2c3920372c"},
+        "src_sha256": "781e22d18925795044f1b4efac107c7980893979c6fc6ffdda905c4c48a1c966"},
 }
 
 
