@@ -71,7 +71,8 @@ def parse():
                         "or the library's choice (auto)")
     p.add_argument("--clock", default="fp32", choices=["fp64", "fp32"], help="ensemble512 only")
     p.add_argument("--study", default=None,
-                   choices=["weak-order", "weak-order-replicas", "clock-error", "nested", "dt-error-scaling"],
+                   choices=["weak-order", "weak-order-replicas", "clock-error", "nested", "dt-error-scaling",
+                            "cpu-ssa"],
                    help="instead of the throughput line: the weak-order study of the 1024^2 Ising "
                         "workload (Lie and Strang, dt in {1, 1/2, 1/4, 1/8} against the dt -> 0 "
                         "limit), or the binary32-vs-binary64 clock error of the workload's observables")
@@ -923,6 +924,39 @@ def study_dt_error_scaling(args):
     print(json.dumps(out), flush=True)
 
 
+def study_cpu_ssa(args):
+    """The serial SSA (the process the splitting approximates) timed on one
+    host core for every workload's model and rates: the class-list form on a
+    256 x 256 lattice (a 65,536-site ring) in slices of one time unit, and
+    the direct-recount form on 32 x 32 (its cost per event grows with the
+    lattice) in slices of dt, until `--cpu-seconds` of wall time; events/s."""
+    import oracle
+    out = {"cores": 1, "workloads": {}}
+    for name, w in WORKLOADS.items():
+        if "lx" not in w:
+            w = ensemble_sample(w, __import__("workloads").ensemble_replicas(w["n"], w["seed"]), (16, 16))
+        row = {}
+        for form, side in (("class_lists", 256), ("direct", 32)):
+            lx, ly = (side * side, 1) if w["model"] == "ISING1D" else (side, side)
+            if "bump" in w:
+                lat = oracle.init_bump(lx, ly, w["seed"], w["bump"]["amp"], lx / 8.0, 1)
+            else:
+                lat = oracle.init_bernoulli(lx, ly, w["seed"], w.get("coverage", 0.5))
+            run = oracle.ssa_bkl_run if form == "class_lists" else oracle.ssa_run
+            slice_t = 1.0 if form == "class_lists" else w["dt"]  # the class lists are rebuilt per call
+            t0 = time.perf_counter()
+            ev = 0
+            k = 0
+            while k == 0 or time.perf_counter() - t0 < args.cpu_seconds:
+                lat, n = run(lx, ly, w["model"], w["rates"], lat, slice_t, w["seed"], replica=k)
+                ev += n
+                k += 1
+            dt = time.perf_counter() - t0
+            row[form] = {"events_per_s": ev / dt, "lattice": f"{lx}x{ly}", "events": ev, "seconds": dt}
+        out["workloads"][name] = row
+    print(json.dumps(out), flush=True)
+
+
 def study_clock_error(args):
     """Binary32 minus binary64 window clock, per observable, on the
     workload's own lattice and schedule: several independent runs of each
@@ -984,6 +1018,9 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.study == "cpu-ssa":
+        study_cpu_ssa(args)
         return
     from paper_1105_4673_gb300 import build as B
     B.build()

@@ -107,3 +107,59 @@ def test_fullsize_ensemble_sampled_replicas():
                          lambda: oracle.FSRun(rp["lx"], rp["ly"], 16, 16, w["model"], rp["rates"], init,
                                               replica=r),
                          w["scheme"], w["dt"], 0.4, seed, replica=r, what=f"replica {r}")
+
+
+def _threads():
+    import os
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_fullsize_ising1024_whole_lattice(engine):
+    """The benchmark's 1024^2 Ising configuration itself -- bit-packed, 4
+    cells per warp, binary64 clock, Lie dt = 1 -- for 8 windows from the
+    workload's own initial state, compared whole (lattice, events, workloads)
+    with the oracle (its all-core form, bit-identical to the one-thread run)."""
+    w = WORKLOADS["ising1024"]
+    lx, ly, q = w["lx"], w["ly"], w["q"]
+    seed = w["seed"]
+    init = oracle.init_bernoulli(lx, ly, seed, w["coverage"])
+    orc = oracle.FSRun(lx, ly, *q, w["model"], w["rates"], init).run_threads(w["scheme"], w["dt"], 4.0, seed,
+                                                                             _threads())
+    with F.Context(lx, ly, w["model"], w["rates"], q, bitpacked=True) as c:
+        c.set_engine(engine)
+        c.init_random(seed, w["coverage"])
+        assert c.info()["lanes_per_cell"] == 8
+        c.run(w["scheme"], w["dt"], 4.0, seed)
+        got = (c.get_state(), c.stats()["events"], c.workload())
+    match_oracle(got, orc, lambda: gpu_ctx(lx, ly, q, w["model"], w["rates"], init, engine=engine, packed=True),
+                 lambda: oracle.FSRun(lx, ly, *q, w["model"], w["rates"], init), w["scheme"], w["dt"], 4.0, seed,
+                 what=f"ising1024 {engine}")
+
+
+@pytest.mark.parametrize("engine", ["PLAIN", "PERSISTENT"])
+def test_fullsize_zgb_bump_whole_lattice(engine):
+    """The headline workload's kernels (32x32 ZGB cells, one per warp,
+    asynchronous row staging, mask write-back) with the binary64 clock on a
+    2048^2 lattice from the same kind of Gaussian bump, Strang dt = 0.02 for
+    10 steps (30 windows), compared whole with the oracle."""
+    w = WORKLOADS["zgb16384"]
+    lx = ly = 2048
+    q = w["q"]
+    seed = w["seed"]
+    init = oracle.init_bump(lx, ly, seed, w["bump"]["amp"], lx / 8.0, 1)
+    orc = oracle.FSRun(lx, ly, *q, w["model"], w["rates"], init).run_threads(w["scheme"], w["dt"], 0.2, seed,
+                                                                             _threads())
+    with F.Context(lx, ly, w["model"], w["rates"], q) as c:
+        c.set_engine(engine)
+        c.init_bump(seed, w["bump"]["amp"], lx / 8.0, 1)
+        assert np.array_equal(c.get_state(), init)
+        c.run(w["scheme"], w["dt"], 0.2, seed)
+        got = (c.get_state(), c.stats()["events"], c.workload())
+    assert got[1] > 5 * 10 ** 5
+    match_oracle(got, orc, lambda: gpu_ctx(lx, ly, q, w["model"], w["rates"], init, engine=engine),
+                 lambda: oracle.FSRun(lx, ly, *q, w["model"], w["rates"], init), w["scheme"], w["dt"], 0.2, seed,
+                 what=f"zgb 2048^2 {engine}")
