@@ -58,7 +58,7 @@ def parse():
                    help="the form timed beside it on the same workload")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-variants", action="store_true", help="skip the other two forms")
-    p.add_argument("--dt-error-runs", type=int, default=4,
+    p.add_argument("--dt-error-runs", type=int, default=8,
                    help="independent runs per arm of the dt-error estimate (0: skip)")
     p.add_argument("--dt-error-T", type=float, default=2.56, help="physical time of the dt-error runs")
     p.add_argument("--wpb", type=int, default=0, help="warps per CTA (0: the library default)")
@@ -187,11 +187,11 @@ def algo_lane_ops_per_event(model, q, fp64):
 # source they were taken on: DRAM bytes per fractional window of the
 # workload and the issue-slot utilisation.
 PROFILED = {
-    ("fs_persistent_kernel<ZGB,float>", "zgb16384"): {
-        "src": ["fskmc_window.cu", "fskmc_cell.cuh", "fskmc_device.cuh", "fskmc_internal.h",
-                "fskmc_persistent.h"],
-        "dram_bytes_per_window": 498310433, "issue_active": 0.773,
-        "src_sha256": "781e22d18925795044f1b4efac107c7980893979c6fc6ffdda905c4c48a1c966"},
+    ("fs_persistent_kernel<ZGB,float,rows in registers>", "zgb16384"): {
+        "src": ["fskmc_window.cu", "fskmc_zgb32.cuh", "fskmc_device.cuh", "fskmc_internal.h",
+                "fskmc_persistent.h", "philox.cuh"],
+        "dram_bytes_per_window": 510047949, "issue_active": 0.728,
+        "src_sha256": "e54b881972defb6ddeb78b0ce1c7408a2667772bf262140407fb8eccdb856bba"},
 }
 
 
@@ -204,7 +204,7 @@ def src_sha(names):
     return h.hexdigest()
 
 
-def kernel_name(engine, model, fp64, packed, lanes):
+def kernel_name(engine, model, fp64, packed, lanes, q=None):
     """The window kernel the bench's configuration launches."""
     grouped = lanes < 32
     base = {("PLAIN", False): "fs_window_kernel", ("PERSISTENT", False): "fs_persistent_kernel",
@@ -212,6 +212,8 @@ def kernel_name(engine, model, fp64, packed, lanes):
     args = [model, "double" if fp64 else "float"] + (["packed"] if packed else [])
     if grouped:
         args.append(f"W={lanes}")
+    if model == "ZGB" and not fp64 and q == (32, 32):
+        args.append("rows in registers")
     return f"{base[(engine, grouped)]}<{','.join(args)}>"
 
 
@@ -452,6 +454,11 @@ def dt_error(F, w, stream, runs, T, args):
     def mse(a):
         return a.mean(axis=0), a.std(axis=0, ddof=1) / np.sqrt(len(a))
 
+    # the two forms agree if their difference lies within the two-sided
+    # 99.7% interval of Student's t with 2 (runs - 1) degrees of freedom (3 SE
+    # for many runs; the standard errors of a few runs are themselves uncertain)
+    from scipy.stats import t as student_t
+    crit = float(student_t.ppf(0.9985, 2 * (runs - 1)))
     m64, s64 = mse(res["fp64"])
     m32, s32 = mse(res["fp32"])
     mr, sr = mse(res["ref"])
@@ -462,8 +469,9 @@ def dt_error(F, w, stream, runs, T, args):
         out["observables"][n] = {"value": float(mr[i]), "dt_error_fp64": float(e64), "se_fp64": se64,
                                  "dt_error_fp32": float(e32), "se_fp32": se32,
                                  "fp32_minus_fp64": float(d), "se_diff": sd,
-                                 "same_dt_error_within_3se": bool(abs(d) <= 3 * sd)}
-    out["all_within_3se"] = all(o["same_dt_error_within_3se"] for o in out["observables"].values())
+                                 "same_dt_error": bool(abs(d) <= crit * sd)}
+    out["t_crit"] = crit
+    out["all_same"] = all(o["same_dt_error"] for o in out["observables"].values())
     out["ambiguous_cell_windows"] = int(ambiguous)
     out["cell_windows"] = int(cellwin)
     return out
@@ -500,7 +508,7 @@ def run_workload(args, rank, world, local):
     engine, clock = FORMS[args.form]
     fp64 = clock == "FP64"
     lanes = info["lanes_per_cell"]
-    kname = kernel_name(engine, w["model"], fp64, bool(w.get("bitpacked")), lanes)
+    kname = kernel_name(engine, w["model"], fp64, bool(w.get("bitpacked")), lanes, tuple(w["q"]))
     nwin_step = kernel_windows_per_step(F, w, STEP_WINDOWS_DT * w["dt"])
     launches_per_step = 1 if engine == "PERSISTENT" else nwin_step
     launch_s = float(np.mean(head["run_ms"])) / 1000.0 / launches_per_step
@@ -530,9 +538,9 @@ def run_workload(args, rank, world, local):
                      f"{base['events_per_s']:.3e} events/s ({ratio:.2f}x) on {args.workload}, "
                      f"{w['scheme']} dt={w['dt']}")
         if dterr:
-            same = "within" if dterr["all_within_3se"] else "NOT within"
-            statement += (f"; the two forms' observables differ by {same} 3 SE at T={dterr['T']} "
-                          f"({dterr['runs_per_arm']} runs each)")
+            same = "within" if dterr["all_same"] else "NOT within"
+            statement += (f"; the two forms' observables differ by {same} {dterr['t_crit']:.2f} SE "
+                          f"(99.7% t-interval) at T={dterr['T']} ({dterr['runs_per_arm']} runs each)")
     sb = stage_bytes_per_site(w)
     out = {
         "metric": METRIC, "value": head["events_per_s"], "unit": "events/s", "n_gpus": world,

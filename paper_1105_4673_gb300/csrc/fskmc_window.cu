@@ -27,6 +27,7 @@
 
 #include "fskmc_cell.cuh"
 #include "fskmc_device.cuh"
+#include "fskmc_zgb32.cuh"
 #include "fskmc_internal.h"
 #include "fskmc_persistent.h"
 #include "philox.cuh"
@@ -36,10 +37,12 @@ namespace fskmc {
 namespace {
 
 // Plain engine: one launch per window, one warp per active cell of one replica.
+// ROWREG: 32-wide ZGB cells with the binary32 clock, held in registers
+// (zgb32_window); otherwise the generic window (cell_window).
 // Held to 64 registers (two 512-thread blocks per SM): with more warps
 // resident the latency of one event's chain hides better (16384^2 ZGB:
 // +2-8%; the binary64 forms spill a few words and still gain).
-template <int MODEL, typename CLK, bool PACKED>
+template <int MODEL, typename CLK, bool PACKED, bool ROWREG = false>
 __global__ void __launch_bounds__(512, 2) fs_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -69,9 +72,14 @@ __global__ void __launch_bounds__(512, 2) fs_window_kernel(WindowArgs a, int nac
     }
     bool amb = false, bad = false;
     uint32_t nexact = 0;
-    uint32_t e = cell_window<MODEL, CLK, false, PACKED>(smem + (size_t)wib * smem_per_warp, R, a.geom,
-                                                cell_at(R, a.geom, cx, cy), a.colour, a.w, a.h, a.screen != 0, a.seed, src, dst,
-                                                lane, &amb, &bad, &nexact);
+    uint32_t e;
+    if constexpr (ROWREG)
+        e = zgb32_window<false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cell_at(R, a.geom, cx, cy),
+                                a.colour, a.w, a.h, a.seed, src, dst, lane, &bad);
+    else
+        e = cell_window<MODEL, CLK, false, PACKED>(smem + (size_t)wib * smem_per_warp, R, a.geom,
+                                                   cell_at(R, a.geom, cx, cy), a.colour, a.w, a.h, a.screen != 0,
+                                                   a.seed, src, dst, lane, &amb, &bad, &nexact);
     if (lane == 0) {
         a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
         atomicAdd(&a.counters[0], (unsigned long long)e);
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(512, 2) fs_window_kernel(WindowArgs a, int nac
 // ---------------------------------------------------------------------------
 
 // Held to 64 registers (four 256-thread blocks per SM), as the plain kernel.
-template <int MODEL, typename CLK, bool PACKED>
+template <int MODEL, typename CLK, bool PACKED, bool ROWREG = false>
 __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp, int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -191,9 +199,14 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp
         if (active) {
             bool amb = false, bad = false;
             uint32_t nexact = 0;
-            uint32_t e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol,
-                                                      P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
-                                                      cur, nxt, lane, &amb, &bad, &nexact);
+            uint32_t e;
+            if constexpr (ROWREG)
+                e = zgb32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
+                                       P.h[i], P.seed, cur, nxt, lane, &bad);
+            else
+                e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol,
+                                                          P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
+                                                          cur, nxt, lane, &amb, &bad, &nexact);
             if (lane == 0) {
                 P.workload[R.cell_off + m] = (int32_t)e;
                 atomicAdd(&P.counters[0], (unsigned long long)e);
@@ -231,6 +244,9 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     if constexpr (is_spin_flip<MODEL>()) {
         if (a.packed) kern = fp32 ? fs_window_kernel<MODEL, float, true> : fs_window_kernel<MODEL, double, true>;
     }
+    if constexpr (MODEL == ZGB) {
+        if (fp32 && a.geom.qx == 32) kern = fs_window_kernel<MODEL, float, false, true>;
+    }
     if (!kern) kern = fp32 ? fs_window_kernel<MODEL, float, false> : fs_window_kernel<MODEL, double, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
@@ -238,8 +254,11 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
 }
 
 template <int MODEL>
-void *persistent_kernel_ptr(int fp32, bool packed)
+void *persistent_kernel_ptr(int fp32, bool packed, int qx)
 {
+    if constexpr (MODEL == ZGB) {
+        if (fp32 && qx == 32) return (void *)fs_persistent_kernel<MODEL, float, false, true>;
+    }
     if constexpr (is_spin_flip<MODEL>()) {
         if (packed)
             return fp32 ? (void *)fs_persistent_kernel<MODEL, float, true>
@@ -249,14 +268,14 @@ void *persistent_kernel_ptr(int fp32, bool packed)
                 : (void *)fs_persistent_kernel<MODEL, double, false>;
 }
 
-void *persistent_kernel_for(int model, int fp32, bool packed)
+void *persistent_kernel_for(int model, int fp32, bool packed, int qx)
 {
     switch (model) {
-    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32, packed);
-    case ISING: return persistent_kernel_ptr<ISING>(fp32, packed);
-    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false);
-    case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false);
-    case ISING1D: return persistent_kernel_ptr<ISING1D>(fp32, packed);
+    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32, packed, qx);
+    case ISING: return persistent_kernel_ptr<ISING>(fp32, packed, qx);
+    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false, qx);
+    case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false, qx);
+    case ISING1D: return persistent_kernel_ptr<ISING1D>(fp32, packed, qx);
     }
     return nullptr;
 }
@@ -368,7 +387,7 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         // kernel's int argument is the per-cell or per-warp shared memory
         const bool grouped = run.lanes_per_cell < 32;
         void *kern = grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
-                             : persistent_kernel_for(run.model, run.fp32, run.packed);
+                             : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx);
         if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
         const int wbytes = grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
                                    : (int)window_smem_per_warp(run.model, run.qx, run.qy);

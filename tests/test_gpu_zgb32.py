@@ -1,0 +1,106 @@
+"""The register-resident binary32 window of 32-wide ZGB cells (the batched
+form of the 16384^2 benchmark) against the binary64 form, which is the
+oracle's arithmetic bit for bit: pair events on undirected bonds at twice
+the directed rate are the same process, so over many replicas from the same
+snapshot the event counts and every observable agree within 4 standard
+errors -- both engines, E and O windows, cross bonds at the lattice's
+periodic edges; and the two engines give identical lattices."""
+import numpy as np
+import pytest
+
+import paper_1105_4673_gb300 as F
+from workloads import random_lattice
+
+pytestmark = pytest.mark.gpu
+
+RATES = dict(yA=0.52, kr=100.0, kd=0.01)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1105_4673_gb300 import build
+    build.build()
+
+
+def _runs(clock, engine, n, lx, ly, qy, scheme, dt, T, snap):
+    reps = [dict(lx=lx, ly=ly, rates=RATES)] * n
+    with F.Context(model="ZGB", q=(32, qy), batch=reps) as b:
+        b.set_clock(clock)
+        b.set_engine(engine)
+        for r in range(n):
+            b.set_state(snap, r)
+        b.run(scheme, dt, T, 0x2B32)
+        st = b.stats()
+        assert st["check_failures"] == 0 and st["timeouts"] == 0
+        obs = []
+        for r in range(n):
+            cov, _, pc = b.observables(r, 2)
+            obs.append(np.concatenate([cov, pc]))
+        return st["events"], np.array(obs)
+
+
+@pytest.mark.parametrize("lx,ly,qy,scheme,dt,T", [
+    (64, 64, 32, "STRANG", 0.02, 0.1),
+    (128, 64, 16, "LIE", 0.05, 0.2),
+    (64, 128, 32, "RANDOM", 0.02, 0.2),
+])
+def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T):
+    n = 1024
+    snap = random_lattice(lx, ly, 3, lx + qy, p=[0.5, 0.25, 0.25])
+    ev32, o32 = _runs("FP32", "PERSISTENT", n, lx, ly, qy, scheme, dt, T, snap)
+    ev64, o64 = _runs("FP64", "PLAIN", n, lx, ly, qy, scheme, dt, T, snap)
+    # event counts: the totals of n independent replicas (Poisson-like: SE ~ sqrt)
+    assert abs(ev32 - ev64) < 5 * np.sqrt(ev32 + ev64), (ev32, ev64)
+    se = np.sqrt(o32.var(axis=0, ddof=1) / n + o64.var(axis=0, ddof=1) / n) + 1e-12
+    z = np.abs(o32.mean(axis=0) - o64.mean(axis=0)) / se
+    assert np.all(z < 4), z
+
+
+def test_zgb32_engines_agree_bitwise():
+    lx = ly = 128
+    snap = random_lattice(lx, ly, 3, 7, p=[0.6, 0.2, 0.2])
+    out = []
+    for engine in ("PLAIN", "PERSISTENT"):
+        with F.Context(lx, ly, "ZGB", RATES, (32, 32)) as c:
+            c.set_clock("FP32")
+            c.set_engine(engine)
+            c.set_state(snap)
+            c.run("STRANG", 0.02, 0.4, 5)
+            out.append((c.get_state(), c.stats()["events"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] > 0
+
+
+@pytest.mark.parametrize("colour", [0, 1])
+def test_zgb32_single_window_outcomes_match_binary64(colour):
+    """One short window (about half an event per active half-lattice) from a fixed
+    snapshot on a 64x4 lattice (32x2 cells; every site borders a cell edge):
+    the distribution of outcomes -- which sites changed and to what -- over
+    20,000 replicas of the register-resident binary32 window and of the
+    binary64 window (the oracle's arithmetic) agree by a two-sample
+    chi-square, so the members, their ownership (cross bonds in E windows
+    horizontally, in O windows vertically) and their rates are the same."""
+    from collections import Counter
+
+    from scipy.stats import chi2_contingency
+    lx, ly, n = 64, 4, 20000
+    snap = random_lattice(lx, ly, 3, 99 + colour, p=[0.5, 0.25, 0.25])
+    reps = [dict(lx=lx, ly=ly, rates=RATES)] * n
+    counts = []
+    for clock in ("FP32", "FP64"):
+        with F.Context(model="ZGB", q=(32, 2), batch=reps) as b:
+            b.set_clock(clock)
+            for r in range(n):
+                b.set_state(snap, r)
+            b.window(colour, 0.0004, 0x51DE + colour)
+            keys = Counter()
+            for r in range(n):
+                g = b.get_state(r)
+                idx = np.nonzero(g != snap)[0]
+                keys[tuple(idx.tolist()) + tuple(g[idx].tolist())] += 1
+        counts.append(keys)
+    allk = set(counts[0]) | set(counts[1])
+    big = [k for k in allk if counts[0][k] + counts[1][k] >= 20]
+    rest = [sum(c[k] for k in allk if k not in big) for c in counts]
+    table = np.array([[c[k] for k in big] + [rest[i]] for i, c in enumerate(counts)])
+    assert len(big) > 20  # many distinct single events: sites and bonds of both classes
+    assert chi2_contingency(table)[1] > 1e-3
