@@ -482,7 +482,9 @@ __device__ bool wait_epochs(const int32_t *ep, int dep, bool has_dep, int target
         __nanosleep(ns);
         if ((spins & 3u) == 0u && ns < 4096u) ns <<= 1;
     }
-    __threadfence();
+    // the relaxed polls that saw the flags and this fence form an acquire;
+    // the warp barrier orders the other lanes' later reads after it
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     __syncwarp();
     return true;
 }

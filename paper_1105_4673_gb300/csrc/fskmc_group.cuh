@@ -638,11 +638,10 @@ __global__ void __launch_bounds__(256) fs_group_kernel(WindowArgs a, int nactive
 // its edge neighbours' last active window before this one (epoch = 1 + last
 // active window) -- with the bounded, backed-off polls of wait_epochs.
 template <int MODEL, typename CLK, bool PACKED, int W>
-__global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams *pp, int stride)
+__global__ void __launch_bounds__(256) fs_group_persistent_kernel(const __grid_constant__ PParams P, int stride)
 {
     constexpr int GC = 32 / W;
     extern __shared__ __align__(16) uint8_t smem[];
-    const PParams &P = *pp;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int gl = lane & (W - 1);
@@ -724,9 +723,10 @@ __global__ void __launch_bounds__(256) fs_group_persistent_kernel(const PParams 
                                                    &nexact);
         if (valid && gl == 0) P.workload[R.cell_off + m] = (int32_t)ev;
         add_counters<W>(P.counters, lane, valid, ev, amb, bad, nexact);
+        // the warp barrier orders the group's writes before its lead lane's
+        // release store (release is cumulative), which publishes them
         __syncwarp();
         if (valid && gl == 0) {
-            __threadfence();
             cuda::atomic_ref<int32_t, cuda::thread_scope_device> ea(ep[m]);
             ea.store(i + 1, cuda::memory_order_release);
         }

@@ -113,7 +113,7 @@ int group_width(int model, int qx, int qy);
 size_t group_smem_per_warp(int model, int qx, int qy);
 // The grouped kernel for (model, clock, storage, cell shape): plain window
 // kernel (args: WindowArgs, int nactive, int stride) or persistent kernel
-// (args: const PParams *, int stride), stride = group_smem_per_warp / (32 / W).
+// (args: PParams by value, int stride), stride = group_smem_per_warp / (32 / W).
 void *group_kernel_for(int model, int fp32, bool packed, int qx, int qy, bool persistent);
 // The same per clock, for W lanes per cell.
 void *group_kernel_f64(int model, bool packed, int lanes, bool persistent);

@@ -19,6 +19,7 @@
 //
 // Lanes own contiguous runs of s = ceil(qx*qy/32) sites in local row-major
 // order, so the canonical member order (site-major, then slot) is lane-major.
+#include <algorithm>
 #include <cuda/atomic>
 #include <cuda_runtime.h>
 
@@ -109,11 +110,13 @@ __global__ void __launch_bounds__(512, 2) fs_window_kernel(WindowArgs a, int nac
 // ---------------------------------------------------------------------------
 
 // Held to 64 registers (four 256-thread blocks per SM), as the plain kernel.
+// The parameters are a kernel argument (constant bank), so the loop reads
+// them without holding them in registers.
 template <int MODEL, typename CLK, bool PACKED, bool ROWREG = false>
-__global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp, int smem_per_warp)
+__global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_constant__ PParams P,
+                                                               int smem_per_warp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
-    const PParams &P = *pp;
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     uint8_t *wsm = smem + (size_t)wib * smem_per_warp;
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp
         }
         const int m = cy * R.ncx + cx;
         int32_t *ep = P.epoch + R.cell_off;
+        const int slot = R.cell_off + m;
         uint8_t *cur = (pingpong && (i & 1)) ? P.lat2 : P.lat;
         uint8_t *nxt = pingpong ? ((i & 1) ? P.lat : P.lat2) : cur;
         cur += R.lat_off;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp
                                                           P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
                                                           cur, nxt, lane, &amb, &bad, &nexact);
             if (lane == 0) {
-                P.workload[R.cell_off + m] = (int32_t)e;
+                P.workload[slot] = (int32_t)e;
                 atomicAdd(&P.counters[0], (unsigned long long)e);
                 if (amb) atomicAdd(&P.counters[1], 1ull);
                 if (bad) atomicAdd(&P.counters[3], 1ull);
@@ -223,10 +227,11 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const PParams *pp
             ok = wait_epochs(ep, ncy2 * R.ncx + ncx2, lane < 4, i + 1, P, lane);
             if (!ok) break;
         }
+        // the warp barrier orders every lane's writes before lane 0's release
+        // store (release is cumulative), which publishes them
         __syncwarp();
         if (lane == 0) {
-            __threadfence();
-            cuda::atomic_ref<int32_t, cuda::thread_scope_device> ea(ep[m]);
+            cuda::atomic_ref<int32_t, cuda::thread_scope_device> ea(P.epoch[slot]);
             ea.store(i + 1, cuda::memory_order_release);
         }
     }
@@ -236,7 +241,8 @@ template <int MODEL>
 cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
 {
     if (a.lanes_per_cell < 32) return launch_group_window(MODEL, fp32, a, nactive, wpb, st);
-    const int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
+    int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
+    if constexpr (MODEL == ZGB) spw = std::max(spw, zgb32_smem(a.geom.qy));  // either window fits
     size_t smem = (size_t)spw * wpb;
     int blocks = (nactive + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
@@ -245,7 +251,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
         if (a.packed) kern = fp32 ? fs_window_kernel<MODEL, float, true> : fs_window_kernel<MODEL, double, true>;
     }
     if constexpr (MODEL == ZGB) {
-        if (fp32 && a.geom.qx == 32) kern = fs_window_kernel<MODEL, float, false, true>;
+        if (fp32 && a.geom.qx == 32 && a.geom.qy >= 2) kern = fs_window_kernel<MODEL, float, false, true>;
     }
     if (!kern) kern = fp32 ? fs_window_kernel<MODEL, float, false> : fs_window_kernel<MODEL, double, false>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -254,10 +260,10 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
 }
 
 template <int MODEL>
-void *persistent_kernel_ptr(int fp32, bool packed, int qx)
+void *persistent_kernel_ptr(int fp32, bool packed, int qx, int qy)
 {
     if constexpr (MODEL == ZGB) {
-        if (fp32 && qx == 32) return (void *)fs_persistent_kernel<MODEL, float, false, true>;
+        if (fp32 && qx == 32 && qy >= 2) return (void *)fs_persistent_kernel<MODEL, float, false, true>;
     }
     if constexpr (is_spin_flip<MODEL>()) {
         if (packed)
@@ -268,14 +274,14 @@ void *persistent_kernel_ptr(int fp32, bool packed, int qx)
                 : (void *)fs_persistent_kernel<MODEL, double, false>;
 }
 
-void *persistent_kernel_for(int model, int fp32, bool packed, int qx)
+void *persistent_kernel_for(int model, int fp32, bool packed, int qx, int qy)
 {
     switch (model) {
-    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32, packed, qx);
-    case ISING: return persistent_kernel_ptr<ISING>(fp32, packed, qx);
-    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false, qx);
-    case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false, qx);
-    case ISING1D: return persistent_kernel_ptr<ISING1D>(fp32, packed, qx);
+    case ADSDES: return persistent_kernel_ptr<ADSDES>(fp32, packed, qx, qy);
+    case ISING: return persistent_kernel_ptr<ISING>(fp32, packed, qx, qy);
+    case DIFFUSION: return persistent_kernel_ptr<DIFFUSION>(fp32, false, qx, qy);
+    case ZGB: return persistent_kernel_ptr<ZGB>(fp32, false, qx, qy);
+    case ISING1D: return persistent_kernel_ptr<ISING1D>(fp32, packed, qx, qy);
     }
     return nullptr;
 }
@@ -288,7 +294,7 @@ size_t window_smem_per_warp(int model, int qx, int qy)
     case ADSDES: return make_layout<ADSDES>(qx, qy).bytes;
     case ISING: return make_layout<ISING>(qx, qy).bytes;
     case DIFFUSION: return make_layout<DIFFUSION>(qx, qy).bytes;
-    case ZGB: return make_layout<ZGB>(qx, qy).bytes;
+    case ZGB: return std::max(make_layout<ZGB>(qx, qy).bytes, zgb32_smem(qy));
     case ISING1D: return make_layout<ISING1D>(qx, qy).bytes;
     }
     return 0;
@@ -311,7 +317,11 @@ cudaError_t launch_window(int model, int fp32, const WindowArgs &a, int nactive,
 // reset the per-cell epochs and the queue, then run the persistent kernel.
 struct PersistentState {
     int model = -1, fp32 = -1, wpb = -1, grid = 0, packed = -1, lanes = -1;
-    PParams *d_params = nullptr;
+    // the kernel node of the graph, whose PParams argument is set before each launch
+    cudaGraphNode_t knode = nullptr;
+    void *kern = nullptr;
+    int spw = 0;
+    size_t smem = 0;
     int32_t *d_epoch = nullptr;
     unsigned long long *d_queue = nullptr;  // [0] queue, [1] abort flag (low word)
     int32_t *d_prefix = nullptr;
@@ -333,7 +343,6 @@ void persistent_free(PersistentState *st)
     if (!st) return;
     if (st->exec) cudaGraphExecDestroy(st->exec);
     if (st->graph) cudaGraphDestroy(st->graph);
-    cudaFree(st->d_params);
     cudaFree(st->d_epoch);
     cudaFree(st->d_queue);
     cudaFree(st->d_prefix);
@@ -359,7 +368,6 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     if (!st) {
         st = new PersistentState();
         *pst = st;
-        PCK(cudaMalloc(&st->d_params, sizeof(PParams)));
         PCK(cudaMalloc(&st->d_epoch, sizeof(int32_t) * (size_t)run.total_cells));
         PCK(cudaMalloc(&st->d_queue, 2 * sizeof(unsigned long long)));
         PCK(cudaMalloc(&st->d_prefix, sizeof(int32_t) * (size_t)(run.nrep + 1)));
@@ -377,46 +385,6 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         PCK(cudaMemcpyAsync(st->d_cell_rk, rk.data(), sizeof(int2) * rk.size(), cudaMemcpyHostToDevice, s));
         PCK(cudaStreamSynchronize(s));  // the host vectors go out of scope
         st->total_cells = run.total_cells;
-    }
-    // (Re)build the graph when the kernel variant or launch shape changes.
-    if (st->model != run.model || st->fp32 != run.fp32 || st->wpb != run.wpb ||
-        st->packed != (int)run.packed || st->lanes != run.lanes_per_cell) {
-        if (st->exec) { cudaGraphExecDestroy(st->exec); st->exec = nullptr; }
-        if (st->graph) { cudaGraphDestroy(st->graph); st->graph = nullptr; }
-        // grouped kernel (several cells per warp) or one cell per warp; the
-        // kernel's int argument is the per-cell or per-warp shared memory
-        const bool grouped = run.lanes_per_cell < 32;
-        void *kern = grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
-                             : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx);
-        if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
-        const int wbytes = grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
-                                   : (int)window_smem_per_warp(run.model, run.qx, run.qy);
-        const int spw = grouped ? wbytes / (32 / run.lanes_per_cell) : wbytes;
-        const size_t smem = (size_t)wbytes * run.wpb;
-        PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0, dev = 0, nsm = 0;
-        PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * run.wpb, smem));
-        PCK(cudaGetDevice(&dev));
-        PCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        if (per_sm < 1) { *msg = "persistent kernel does not fit on an SM"; return cudaErrorInvalidConfiguration; }
-        st->grid = per_sm * nsm;
-        cudaStream_t cs;
-        PCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        PCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(st->d_epoch, 0, sizeof(int32_t) * (size_t)st->total_cells, cs);
-        cudaMemsetAsync(st->d_queue, 0, 2 * sizeof(unsigned long long), cs);
-        const PParams *pp = st->d_params;
-        void *args[] = {(void *)&pp, (void *)&spw};
-        cudaLaunchKernel(kern, dim3(st->grid), dim3(32 * run.wpb), args, smem, cs);
-        cudaError_t ce = cudaStreamEndCapture(cs, &st->graph);
-        cudaStreamDestroy(cs);
-        if (ce != cudaSuccess) { *msg = "graph capture"; return ce; }
-        PCK(cudaGraphInstantiate(&st->exec, st->graph, 0));
-        st->model = run.model;
-        st->fp32 = run.fp32;
-        st->wpb = run.wpb;
-        st->packed = (int)run.packed;
-        st->lanes = run.lanes_per_cell;
     }
     const size_t ncol = (size_t)run.nwin * (run.colour_per_replica ? run.nrep : 1);
     if (ncol > st->colour_cap) {
@@ -477,7 +445,72 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
     P.epoch = st->d_epoch;
     P.queue = st->d_queue;
     P.abort_flag = reinterpret_cast<int32_t *>(st->d_queue + 1);
-    PCK(cudaMemcpyAsync(st->d_params, &P, sizeof P, cudaMemcpyHostToDevice, s));
+    // (Re)build the graph when the kernel variant or launch shape changes;
+    // otherwise set this run's parameters on its kernel node.
+    if (st->model != run.model || st->fp32 != run.fp32 || st->wpb != run.wpb ||
+        st->packed != (int)run.packed || st->lanes != run.lanes_per_cell) {
+        if (st->exec) { cudaGraphExecDestroy(st->exec); st->exec = nullptr; }
+        if (st->graph) { cudaGraphDestroy(st->graph); st->graph = nullptr; }
+        // grouped kernel (several cells per warp) or one cell per warp; the
+        // kernel's int argument is the per-cell or per-warp shared memory
+        const bool grouped = run.lanes_per_cell < 32;
+        void *kern = grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
+                             : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy);
+        if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
+        const int wbytes = grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
+                                   : (int)window_smem_per_warp(run.model, run.qx, run.qy);
+        const int spw = grouped ? wbytes / (32 / run.lanes_per_cell) : wbytes;
+        const size_t smem = (size_t)wbytes * run.wpb;
+        PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0, dev = 0, nsm = 0;
+        PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * run.wpb, smem));
+        PCK(cudaGetDevice(&dev));
+        PCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        if (per_sm < 1) { *msg = "persistent kernel does not fit on an SM"; return cudaErrorInvalidConfiguration; }
+        st->grid = per_sm * nsm;
+        cudaStream_t cs;
+        PCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        PCK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(st->d_epoch, 0, sizeof(int32_t) * (size_t)st->total_cells, cs);
+        cudaMemsetAsync(st->d_queue, 0, 2 * sizeof(unsigned long long), cs);
+        int spw_arg = spw;
+        void *args[] = {(void *)&P, (void *)&spw_arg};
+        cudaLaunchKernel(kern, dim3(st->grid), dim3(32 * run.wpb), args, smem, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &st->graph);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess) { *msg = "graph capture"; return ce; }
+        PCK(cudaGraphInstantiate(&st->exec, st->graph, 0));
+        size_t nn = 0;
+        PCK(cudaGraphGetNodes(st->graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        PCK(cudaGraphGetNodes(st->graph, nodes.data(), &nn));
+        st->knode = nullptr;
+        for (cudaGraphNode_t n : nodes) {
+            cudaGraphNodeType ty;
+            PCK(cudaGraphNodeGetType(n, &ty));
+            if (ty == cudaGraphNodeTypeKernel) st->knode = n;
+        }
+        if (!st->knode) { *msg = "graph capture: no kernel node"; return cudaErrorUnknown; }
+        st->kern = kern;
+        st->spw = spw;
+        st->smem = smem;
+        st->model = run.model;
+        st->fp32 = run.fp32;
+        st->wpb = run.wpb;
+        st->packed = (int)run.packed;
+        st->lanes = run.lanes_per_cell;
+    } else {
+        int spw_arg = st->spw;
+        void *args[] = {(void *)&P, (void *)&spw_arg};
+        cudaKernelNodeParams kp = {};
+        kp.func = st->kern;
+        kp.gridDim = dim3(st->grid);
+        kp.blockDim = dim3(32 * st->wpb);
+        kp.sharedMemBytes = (unsigned)st->smem;
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        PCK(cudaGraphExecKernelNodeSetParams(st->exec, st->knode, &kp));
+    }
     PCK(cudaGraphLaunch(st->exec, s));
     PCK(cudaMemcpyAsync(st->h_abort, P.abort_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PCK(cudaStreamSynchronize(s));

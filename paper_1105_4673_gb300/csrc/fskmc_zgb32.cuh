@@ -83,7 +83,8 @@ __device__ __forceinline__ void zgb_store_row(uint8_t *p, uint32_t e, uint32_t a
 // V vertical bonds below it (bit x: (x, y)-(x, y+1)), N (lane 0) vertical
 // bonds to the top halo, L (bit 0) the left cross bond. e, a: row y; eB,
 // aB: the row below (the bottom halo row for the last row); eN, aN: the top
-// halo row; hl*, hr*: the row's left and right halo sites (0/1); ew: an E
+// halo row (read in lane 0 only); hl*, hr*: the row's left and right halo
+// sites (0/1); ew: an E
 // window (horizontal cross bonds owned), otherwise an O window (vertical
 // cross bonds owned). Rows without sites (lanes >= qy) have e = a = 0 and
 // row = false.
@@ -124,11 +125,29 @@ __device__ __forceinline__ int zgb_bond_count(const ZgbBonds &B)
     return __popc(B.H) + __popc(B.V) + __popc(B.N) + (int)B.L;
 }
 
-// One cell's binary32-clock window (qx == 32, qy <= 32), the cell at `at`
-// in the byte lattice src (== dst: ZGB updates in place). wsm: 64 * (qy + 2)
-// bytes of 16-byte aligned shared memory for staging. Returns the events;
-// *bad_out is set if a rank search found no member (never, unless the
-// counts and masks disagree) or a window ran away.
+// The per-window constants of zgb32_window, in shared memory behind the
+// staging rows and read (volatile) where they are used, so that across the
+// event loop the registers hold only the cell's state.
+struct alignas(16) Zgb32Const {
+    uint64_t rq[4];  // the class rates in fixed point, the pair classes' doubled (undirected bonds)
+    uint64_t seed;
+    uint8_t *dst;
+    float qscale, hf;
+    uint32_t ctr3, w, m;
+    int32_t X0, Y0, lx, ly;
+};
+
+// Shared memory zgb32_window needs per warp.
+__host__ __device__ constexpr int zgb32_smem(int qy)
+{
+    return 64 * (qy + 2) + (int)sizeof(Zgb32Const);
+}
+
+// One cell's binary32-clock window (qx == 32, 2 <= qy <= 32), the cell at `at`
+// in the byte lattice src (== dst: ZGB updates in place). wsm: zgb32_smem(qy)
+// bytes of 16-byte aligned shared memory. Returns the events; *bad_out is
+// set if a rank search found no member (never, unless the counts and masks
+// disagree) or a window ran away.
 template <bool PERSIST>
 __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom &G, const CellAt &at,
                                  int colour, uint32_t w, double hwin, uint64_t seed, const uint8_t *src,
@@ -136,7 +155,6 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
 {
     constexpr unsigned FULLW = 0xffffffffu;
     const int qy = G.qy, BH = qy + 2;
-    const int lx = at.lx, ly = at.ly, X0 = at.X0, Y0 = at.Y0;
     const bool ew = colour == 0;
     const bool row = lane < qy, first = lane == 0, last = lane == qy - 1;
 
@@ -144,20 +162,43 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
     // aligned 16-byte chunks -- the 16 sites left of the cell, its 32, the 16
     // right of it -- all in flight at once.
     uint8_t *raw = wsm;
-    const int xl = X0 >= 16 ? X0 - 16 : X0 - 16 + lx;
-    const int xr = X0 + 32 < lx ? X0 + 32 : X0 + 32 - lx;
-    for (int i = lane; i < 4 * BH; i += 32) {
-        const int by = i >> 2, part = i & 3;
-        int gy = Y0 - 1 + by;
-        gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
-        const int gx = part == 0 ? xl : (part == 3 ? xr : X0 + 16 * (part - 1));
-        cp_async16(raw + by * 64 + 16 * part, src + (int64_t)gy * lx + gx);
+    {
+        const int lx = at.lx, ly = at.ly, X0 = at.X0, Y0 = at.Y0;
+        const int xl = X0 >= 16 ? X0 - 16 : X0 - 16 + lx;
+        const int xr = X0 + 32 < lx ? X0 + 32 : X0 + 32 - lx;
+        for (int i = lane; i < 4 * BH; i += 32) {
+            const int by = i >> 2, part = i & 3;
+            int gy = Y0 - 1 + by;
+            gy += (gy < 0) ? ly : 0; gy -= (gy >= ly) ? ly : 0;
+            const int gx = part == 0 ? xl : (part == 3 ? xr : X0 + 16 * (part - 1));
+            cp_async16(raw + by * 64 + 16 * part, src + (int64_t)gy * lx + gx);
+        }
+    }
+    Zgb32Const *Cw = reinterpret_cast<Zgb32Const *>(wsm + 64 * BH);
+    if (lane == 0) {
+        Cw->rq[0] = R.rq[0];
+        Cw->rq[1] = 2ull * R.rq[1];
+        Cw->rq[2] = 2ull * R.rq[2];
+        Cw->rq[3] = R.rq[3];
+        Cw->seed = seed;
+        Cw->dst = dst;
+        Cw->qscale = R.qscale;
+        Cw->hf = (float)hwin;
+        Cw->ctr3 = R.rep | (TAG_EVENT << 24);
+        Cw->w = w;
+        Cw->m = at.m;
+        Cw->X0 = at.X0;
+        Cw->Y0 = at.Y0;
+        Cw->lx = at.lx;
+        Cw->ly = at.ly;
     }
     cp_async_wait_all();
     __syncwarp();
-    // lane y: row y (box row y + 1) and its halo sites; lane 0 also the top
-    // halo row, the last lane the bottom halo row
-    uint32_t e = 0u, a = 0u, eN = 0u, aN = 0u, eS = 0u, aS = 0u;
+    const volatile Zgb32Const &C = *Cw;
+    // lane y: row y (box row y + 1) and its halo sites; (eH, aH): in lane 0
+    // the top halo row, in the last lane the bottom halo row (qy >= 2: two
+    // different lanes)
+    uint32_t e = 0u, a = 0u, eH = 0u, aH = 0u;
     uint32_t hle = 0u, hla = 0u, hre = 0u, hra = 0u;
     if (row) {
         const uint8_t *rr = raw + (lane + 1) * 64 + 16;
@@ -165,37 +206,33 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
         hle = rr[-1] == 0; hla = rr[-1] == 1;
         hre = rr[32] == 0; hra = rr[32] == 1;
     }
-    if (first) zgb_row_masks(raw + 16, eN, aN);
-    if (last) zgb_row_masks(raw + (qy + 1) * 64 + 16, eS, aS);
+    if (first) zgb_row_masks(raw + 16, eH, aH);
+    if (last) zgb_row_masks(raw + (qy + 1) * 64 + 16, eH, aH);
 
-    const uint64_t rq0 = R.rq[0], rq1 = 2ull * R.rq[1], rq2 = 2ull * R.rq[2], rq3 = R.rq[3];
-    const float qscale = R.qscale;
-    const float hf = (float)hwin;
-    const uint32_t ctr3 = R.rep | (TAG_EVENT << 24);
     float tauf = 0.0f, rlf = 0.0f;
     uint32_t rw2 = 0u, rw3 = 0u, ev = 0u;
     for (;;) {
         // the classes of the current state: each lane's member counts, the
         // totals (every lane) and the fixed-point rate sums
         uint32_t eB = __shfl_down_sync(FULLW, e, 1), aB = __shfl_down_sync(FULLW, a, 1);
-        if (last) { eB = eS; aB = aS; }
+        if (last) { eB = eH; aB = aH; }
         int cl[4];
         cl[0] = __popc(e);
         cl[3] = __popc(a);
-        cl[1] = zgb_bond_count(zgb_bonds(1, row, last, first, ew, e, a, eB, aB, eN, aN, hle, hla, hre, hra));
-        cl[2] = zgb_bond_count(zgb_bonds(2, row, last, first, ew, e, a, eB, aB, eN, aN, hle, hla, hre, hra));
+        cl[1] = zgb_bond_count(zgb_bonds(1, row, last, first, ew, e, a, eB, aB, eH, aH, hle, hla, hre, hra));
+        cl[2] = zgb_bond_count(zgb_bonds(2, row, last, first, ew, e, a, eB, aB, eH, aH, hle, hla, hre, hra));
         uint32_t n[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) n[k] = __reduce_add_sync(FULLW, (uint32_t)cl[k]);
-        const uint64_t P0 = (uint64_t)n[0] * rq0, P1 = P0 + (uint64_t)n[1] * rq1;
-        const uint64_t P2 = P1 + (uint64_t)n[2] * rq2, lami = P2 + (uint64_t)n[3] * rq3;
+        const uint64_t P0 = (uint64_t)n[0] * C.rq[0], P1 = P0 + (uint64_t)n[1] * C.rq[1];
+        const uint64_t P2 = P1 + (uint64_t)n[2] * C.rq[2], lami = P2 + (uint64_t)n[3] * C.rq[3];
         if (lami == 0ull) break;
         if (ev >= MAX_EVENTS_PER_WINDOW) {
             *bad_out = true;
             break;
         }
         if ((ev & 31u) == 0u) {  // 32 events' draws at once, one Philox block per lane
-            const u32x4 o = draw(seed, ev + (uint32_t)lane, w, at.m, ctr3);
+            const u32x4 o = draw(C.seed, ev + (uint32_t)lane, C.w, C.m, C.ctr3);
             rlf = -__logf(__fmul_rn(__uint2float_rn((o.x >> 8) + 1u), 0x1p-24f));
             rw2 = o.z;
             rw3 = o.w;
@@ -203,9 +240,9 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
         const int sl = (int)(ev & 31u);
         const float l = __shfl_sync(FULLW, rlf, sl);
         const uint32_t w2 = __shfl_sync(FULLW, rw2, sl), w3 = __shfl_sync(FULLW, rw3, sl);
-        const float lamf = __fmul_rn(u64_to_float_rz(lami), qscale);
+        const float lamf = __fmul_rn(u64_to_float_rz(lami), C.qscale);
         const float end = __fadd_rn(tauf, __fdividef(l, lamf));
-        if (end >= hf) break;
+        if (end >= C.hf) break;
         tauf = end;
         // class: the first k with (w2 lambda) >> 32 < P_k (exact integers)
         const uint64_t t = (uint64_t)w2 * (lami >> 32) + (((uint64_t)w2 * (lami & 0xffffffffull)) >> 32);
@@ -236,7 +273,7 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
                 kind = 0;
                 x = select_bit(k == 0 ? e : a, r);
             } else {
-                const ZgbBonds B = zgb_bonds(k, row, last, first, ew, e, a, eB, aB, eN, aN, hle, hla, hre, hra);
+                const ZgbBonds B = zgb_bonds(k, row, last, first, ew, e, a, eB, aB, eH, aH, hle, hla, hre, hra);
                 const int ph = __popc(B.H), pv = __popc(B.V);
                 if (r < ph) { kind = 1; x = select_bit(B.H, r); }
                 else if (r < ph + pv) { kind = 2; x = select_bit(B.V, r - ph); }
@@ -270,8 +307,7 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
                 a &= ~m0;
                 if (hr1) { hre = toB ? 0u : 1u; hra = 0u; }
                 if (hl1) { hle = toB ? 0u : 1u; hla = 0u; }
-                if (top1) { eN = toB ? (eN & ~bit) : (eN | bit); aN &= ~bit; }
-                if (bot1) { eS = toB ? (eS & ~bit) : (eS | bit); aS &= ~bit; }
+                if (top1 || bot1) { eH = toB ? (eH & ~bit) : (eH | bit); aH &= ~bit; }
             }
             if (kind == 2 && !bot1 && lane == y + 1) {
                 e = toB ? (e & ~m1) : (e | m1);
@@ -283,17 +319,19 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
 
     // Write back: the cell's rows, and the owned halo ends (the halo columns
     // in E windows, the halo rows in O windows)
-    if (row) zgb_store_row(dst + (int64_t)(Y0 + lane) * lx + X0, e, a);
+    uint8_t *const out = C.dst;
+    const int lx = C.lx, ly = C.ly, X0 = C.X0, Y0 = C.Y0;
+    if (row) zgb_store_row(out + (int64_t)(Y0 + lane) * lx + X0, e, a);
     if (ew) {
         if (row) {
             const int gy = Y0 + lane;
             const int gxl = X0 > 0 ? X0 - 1 : lx - 1, gxr = X0 + 32 < lx ? X0 + 32 : 0;
-            dst[(int64_t)gy * lx + gxl] = (uint8_t)(hle ? 0 : (hla ? 1 : 2));
-            dst[(int64_t)gy * lx + gxr] = (uint8_t)(hre ? 0 : (hra ? 1 : 2));
+            out[(int64_t)gy * lx + gxl] = (uint8_t)(hle ? 0 : (hla ? 1 : 2));
+            out[(int64_t)gy * lx + gxr] = (uint8_t)(hre ? 0 : (hra ? 1 : 2));
         }
     } else {
-        if (first) zgb_store_row(dst + (int64_t)(Y0 > 0 ? Y0 - 1 : ly - 1) * lx + X0, eN, aN);
-        if (last) zgb_store_row(dst + (int64_t)(Y0 + qy < ly ? Y0 + qy : 0) * lx + X0, eS, aS);
+        if (first) zgb_store_row(out + (int64_t)(Y0 > 0 ? Y0 - 1 : ly - 1) * lx + X0, eH, aH);
+        if (last) zgb_store_row(out + (int64_t)(Y0 + qy < ly ? Y0 + qy : 0) * lx + X0, eH, aH);
     }
     return ev;
 }
