@@ -207,12 +207,14 @@ def src_sha(names):
 def kernel_name(engine, model, fp64, packed, lanes, q=None):
     """The window kernel the bench's configuration launches."""
     grouped = lanes < 32
+    if model == "ZGB" and grouped:  # two 32-wide cells per warp, binary32 clock
+        return {"PLAIN": "fs_zgbp_window_kernel", "PERSISTENT": "fs_zgbp_persistent_kernel"}[engine]
     base = {("PLAIN", False): "fs_window_kernel", ("PERSISTENT", False): "fs_persistent_kernel",
             ("PLAIN", True): "fs_group_kernel", ("PERSISTENT", True): "fs_group_persistent_kernel"}
     args = [model, "double" if fp64 else "float"] + (["packed"] if packed else [])
     if grouped:
         args.append(f"W={lanes}")
-    if model == "ZGB" and not fp64 and q == (32, 32):
+    if model == "ZGB" and not fp64 and q is not None and q[0] == 32 and q[1] >= 2:
         args.append("rows in registers")
     return f"{base[(engine, grouped)]}<{','.join(args)}>"
 

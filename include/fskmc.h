@@ -163,16 +163,17 @@ fskmc_status fskmc_set_engine(fskmc_ctx *ctx, fskmc_engine engine);
    depend on it. */
 fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
 
-/* Cells per warp for the spin-flip models (ADSDES, ISING, ISING1D).
-   mode = 1: a cell of at most 512 sites takes W = 4, 8 or 16 lanes (its
-   32-site words rounded up to a power of two; at least 8 in 2D, 4 on a
-   ring) and a warp runs 32/W cells of the same window in lockstep, so each
-   instruction of the event loop (Eqs. totalrate and skeleton per cell)
-   serves 32/W cells. mode = 0: one cell per warp. mode = 2 (default,
-   auto): the same as 1 (grouped cells were faster in every engine and clock
-   measured). The two-site models and larger cells always take a whole
-   warp. Results (lattices, event counts, workloads) do not depend on the
-   mode. EINVAL: mode outside 0..2. */
+/* Cells per warp. Spin-flip models (ADSDES, ISING, ISING1D), mode = 1: a
+   cell of at most 512 sites takes W = 4, 8 or 16 lanes (its 32-site words
+   rounded up to a power of two; at least 8 in 2D, 4 on a ring) and a warp
+   runs 32/W cells of the same window in lockstep, so each instruction of
+   the event loop (Eqs. totalrate and skeleton per cell) serves 32/W cells.
+   ZGB with the binary32 clock and 32-wide cells of an even number of rows
+   (4 to 32), mode = 1: two cells per warp, 16 lanes each holding two rows.
+   mode = 0: one cell per warp. mode = 2 (default, auto): the same as 1
+   (faster in every engine and clock measured). Diffusion, ZGB otherwise,
+   and larger cells always take a whole warp. Results (lattices, event
+   counts, workloads) do not depend on the mode. EINVAL: mode outside 0..2. */
 fskmc_status fskmc_set_cell_grouping(fskmc_ctx *ctx, int32_t mode);
 
 /* Binary64 clock: how the window-edge decision of each event (Eq. skeleton:

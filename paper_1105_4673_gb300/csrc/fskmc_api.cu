@@ -410,8 +410,13 @@ constexpr int ORDER_GROUP = 1024;
 // clock on the spin-flip workloads).
 int lanes_per_cell(const fskmc_ctx *c)
 {
+    if (c->grouping == 0) return 32;
+    // ZGB, 32-wide cells of an even number of rows, binary32 clock: two
+    // cells per warp, 16 lanes each (fskmc_zgbpair.cu)
+    if (c->model == FSKMC_ZGB)
+        return (c->clock == FSKMC_CLOCK_FP32 && fskmc::zgb_pair_shape(c->qx, c->qy)) ? 16 : 32;
     const int W = fskmc::group_width(c->model, c->qx, c->qy);
-    return (W >= 32 || c->grouping == 0) ? 32 : W;
+    return W >= 32 ? 32 : W;
 }
 
 bool use_order(const fskmc_ctx *c, int64_t active, bool persistent)
@@ -688,8 +693,10 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *c, int32_t warps)
 {
     if (!c) return FSKMC_EINVAL;
     if (warps < 1 || warps > 16) return fail(c, FSKMC_EINVAL, "warps per block must be 1..16");
-    size_t need = std::max(fskmc::window_smem_per_warp(c->model, c->qx, c->qy),
-                           fskmc::group_smem_per_warp(c->model, c->qx, c->qy)) * (size_t)warps;
+    size_t need = std::max({fskmc::window_smem_per_warp(c->model, c->qx, c->qy),
+                            fskmc::group_smem_per_warp(c->model, c->qx, c->qy),
+                            c->model == FSKMC_ZGB ? fskmc::zgb_pair_smem_per_warp(c->qy) : (size_t)0}) *
+                  (size_t)warps;
     if (need > 200 * 1024) return fail(c, FSKMC_EINVAL, "%d warps need %zu B of shared memory", warps, need);
     c->wpb = warps;
     return FSKMC_OK;

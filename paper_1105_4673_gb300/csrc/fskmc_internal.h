@@ -102,6 +102,14 @@ cudaError_t launch_nested(int model, int fp32, const NestedArgs &a, int nsuper_a
 
 // Shared-memory bytes one warp of the window kernel needs.
 size_t window_smem_per_warp(int model, int qx, int qy);
+// The two-cells-per-warp ZGB window with the binary32 clock
+// (fskmc_zgbpair.cu): whether a cell shape takes it, its shared memory per
+// warp, its one-window launch (pairs of active cells, wpb warps per CTA) and
+// its persistent kernel (args: PParams by value, int shared bytes per warp).
+bool zgb_pair_shape(int qx, int qy);
+size_t zgb_pair_smem_per_warp(int qy);
+cudaError_t launch_zgb_pair_window(const WindowArgs &a, int nactive, int wpb, cudaStream_t st);
+void *zgb_pair_persistent_kernel();
 
 // Lanes per cell of the grouped window kernels (several small cells per
 // warp, spin-flip models only): the lanes owning the cell's 32-site words,

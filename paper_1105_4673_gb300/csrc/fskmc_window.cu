@@ -240,7 +240,15 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
 template <int MODEL>
 cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
 {
-    if (a.lanes_per_cell < 32) return launch_group_window(MODEL, fp32, a, nactive, wpb, st);
+    if (a.lanes_per_cell < 32) {
+        // ZGB: two 32-wide cells per warp (binary32 clock); the spin-flip
+        // models: the grouped kernels
+        if constexpr (MODEL == ZGB) {
+            if (!fp32 || !zgb_pair_shape(a.geom.qx, a.geom.qy)) return cudaErrorInvalidValue;
+            return launch_zgb_pair_window(a, nactive, wpb, st);
+        }
+        return launch_group_window(MODEL, fp32, a, nactive, wpb, st);
+    }
     int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
     if constexpr (MODEL == ZGB) spw = std::max(spw, zgb32_smem(a.geom.qy));  // either window fits
     size_t smem = (size_t)spw * wpb;
@@ -451,15 +459,24 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         st->packed != (int)run.packed || st->lanes != run.lanes_per_cell) {
         if (st->exec) { cudaGraphExecDestroy(st->exec); st->exec = nullptr; }
         if (st->graph) { cudaGraphDestroy(st->graph); st->graph = nullptr; }
-        // grouped kernel (several cells per warp) or one cell per warp; the
-        // kernel's int argument is the per-cell or per-warp shared memory
+        // grouped kernel (several cells per warp: ZGB's two-cell kernel or
+        // the spin-flip models' groups) or one cell per warp; the kernel's
+        // int argument is the per-cell (spin-flip groups) or per-warp shared
+        // memory
         const bool grouped = run.lanes_per_cell < 32;
-        void *kern = grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
-                             : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy);
+        const bool zpair = grouped && run.model == ZGB;
+        if (zpair && !(run.fp32 && zgb_pair_shape(run.qx, run.qy))) {
+            *msg = "two-cell ZGB kernel: binary32 clock, 32-wide cells of an even number of rows";
+            return cudaErrorInvalidValue;
+        }
+        void *kern = zpair     ? zgb_pair_persistent_kernel()
+                     : grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
+                               : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy);
         if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
-        const int wbytes = grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
-                                   : (int)window_smem_per_warp(run.model, run.qx, run.qy);
-        const int spw = grouped ? wbytes / (32 / run.lanes_per_cell) : wbytes;
+        const int wbytes = zpair     ? (int)zgb_pair_smem_per_warp(run.qy)
+                           : grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
+                                     : (int)window_smem_per_warp(run.model, run.qx, run.qy);
+        const int spw = (grouped && !zpair) ? wbytes / (32 / run.lanes_per_cell) : wbytes;
         const size_t smem = (size_t)wbytes * run.wpb;
         PCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0, dev = 0, nsm = 0;

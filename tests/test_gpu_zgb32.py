@@ -1,10 +1,12 @@
-"""The register-resident binary32 window of 32-wide ZGB cells (the batched
-form of the 16384^2 benchmark) against the binary64 form, which is the
-oracle's arithmetic bit for bit: pair events on undirected bonds at twice
-the directed rate are the same process, so over many replicas from the same
+"""The register-resident binary32 windows of 32-wide ZGB cells (the batched
+form of the 16384^2 benchmark) -- one cell per warp, or two cells per warp
+at two rows per lane -- against the binary64 form, which is the oracle's
+arithmetic bit for bit: pair events on undirected bonds at twice the
+directed rate are the same process, so over many replicas from the same
 snapshot the event counts and every observable agree within 4 standard
 errors -- both engines, E and O windows, cross bonds at the lattice's
-periodic edges; and the two engines give identical lattices."""
+periodic edges; the two engines give identical lattices, and so do the
+one-cell and two-cell windows (same draws, same member numbering)."""
 import numpy as np
 import pytest
 
@@ -22,11 +24,12 @@ def _lib():
     build.build()
 
 
-def _runs(clock, engine, n, lx, ly, qy, scheme, dt, T, snap):
+def _runs(clock, engine, n, lx, ly, qy, scheme, dt, T, snap, grouped=True):
     reps = [dict(lx=lx, ly=ly, rates=RATES)] * n
     with F.Context(model="ZGB", q=(32, qy), batch=reps) as b:
         b.set_clock(clock)
         b.set_engine(engine)
+        b.set_cell_grouping(grouped)
         for r in range(n):
             b.set_state(snap, r)
         b.run(scheme, dt, T, 0x2B32)
@@ -39,15 +42,17 @@ def _runs(clock, engine, n, lx, ly, qy, scheme, dt, T, snap):
         return st["events"], np.array(obs)
 
 
-@pytest.mark.parametrize("lx,ly,qy,scheme,dt,T", [
-    (64, 64, 32, "STRANG", 0.02, 0.1),
-    (128, 64, 16, "LIE", 0.05, 0.2),
-    (64, 128, 32, "RANDOM", 0.02, 0.2),
+@pytest.mark.parametrize("lx,ly,qy,scheme,dt,T,grouped", [
+    (64, 64, 32, "STRANG", 0.02, 0.1, True),
+    (128, 64, 16, "LIE", 0.05, 0.2, True),
+    (64, 128, 32, "RANDOM", 0.02, 0.2, True),
+    (64, 64, 32, "STRANG", 0.02, 0.1, False),   # one cell per warp
+    (64, 40, 5, "LIE", 0.05, 0.2, True),        # odd rows: one cell per warp
 ])
-def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T):
+def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T, grouped):
     n = 1024
     snap = random_lattice(lx, ly, 3, lx + qy, p=[0.5, 0.25, 0.25])
-    ev32, o32 = _runs("FP32", "PERSISTENT", n, lx, ly, qy, scheme, dt, T, snap)
+    ev32, o32 = _runs("FP32", "PERSISTENT", n, lx, ly, qy, scheme, dt, T, snap, grouped)
     ev64, o64 = _runs("FP64", "PLAIN", n, lx, ly, qy, scheme, dt, T, snap)
     # event counts: the totals of n independent replicas (Poisson-like: SE ~ sqrt)
     assert abs(ev32 - ev64) < 5 * np.sqrt(ev32 + ev64), (ev32, ev64)
@@ -56,24 +61,57 @@ def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T
     assert np.all(z < 4), z
 
 
-def test_zgb32_engines_agree_bitwise():
-    lx = ly = 128
-    snap = random_lattice(lx, ly, 3, 7, p=[0.6, 0.2, 0.2])
+@pytest.mark.parametrize("lx,ly,qy,scheme", [
+    (128, 128, 32, "STRANG"), (256, 64, 16, "RANDOM"), (64, 96, 6, "LIE"), (128, 48, 4, "STRANG"),
+    (64, 64, 2, "LIE"),
+])
+def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
+    """Plain and persistent engines, one and two cells per warp: the same
+    lattice, event count and per-cell workloads in all four."""
+    snap = random_lattice(lx, ly, 3, 7 + qy, p=[0.6, 0.2, 0.2])
     out = []
     for engine in ("PLAIN", "PERSISTENT"):
-        with F.Context(lx, ly, "ZGB", RATES, (32, 32)) as c:
-            c.set_clock("FP32")
-            c.set_engine(engine)
-            c.set_state(snap)
-            c.run("STRANG", 0.02, 0.4, 5)
-            out.append((c.get_state(), c.stats()["events"]))
-    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1] > 0
+        for grouped in (True, False):
+            with F.Context(lx, ly, "ZGB", RATES, (32, qy)) as c:
+                c.set_clock("FP32")
+                c.set_engine(engine)
+                c.set_cell_grouping(grouped)
+                pair = grouped and qy % 2 == 0 and qy >= 4
+                assert c.info()["lanes_per_cell"] == (16 if pair else 32)
+                c.set_state(snap)
+                c.run(scheme, 0.02, 0.4, 5)
+                st = c.stats()
+                assert st["check_failures"] == 0
+                out.append((c.get_state(), st["events"], c.workload()))
+    for g, ev, wl in out[1:]:
+        assert np.array_equal(g, out[0][0]) and ev == out[0][1] > 0 and np.array_equal(wl, out[0][2])
+
+
+def test_zgb32_two_cells_per_warp_batch_equals_one_cell():
+    """A batch of replicas of different sizes and rates in the persistent
+    engine: two cells per warp equals one cell per warp, replica by replica."""
+    reps = [dict(lx=64, ly=64, rates=RATES), dict(lx=128, ly=64, rates=dict(yA=0.45, kr=20.0, kd=0.1)),
+            dict(lx=64, ly=128, rates=dict(yA=0.6, kr=5.0, kd=0.0))]
+    res = []
+    for grouped in (True, False):
+        with F.Context(model="ZGB", q=(32, 16), batch=reps) as b:
+            b.set_clock("FP32")
+            b.set_engine("PERSISTENT")
+            b.set_cell_grouping(grouped)
+            b.init_random(11, 0.5)
+            b.run("RANDOM", 0.05, 0.5, 11)
+            res.append(([b.get_state(r) for r in range(len(reps))], b.stats()["events"]))
+    assert res[0][1] == res[1][1] > 0
+    for r in range(len(reps)):
+        assert np.array_equal(res[0][0][r], res[1][0][r]), f"replica {r}"
 
 
 @pytest.mark.parametrize("colour", [0, 1])
-def test_zgb32_single_window_outcomes_match_binary64(colour):
-    """One short window (about half an event per active half-lattice) from a fixed
-    snapshot on a 64x4 lattice (32x2 cells; every site borders a cell edge):
+@pytest.mark.parametrize("qy", [2, 4])  # one cell per warp; two cells per warp
+def test_zgb32_single_window_outcomes_match_binary64(colour, qy):
+    """One short window (about an event per active half-lattice) from a fixed
+    snapshot on a 64 x 2qy lattice (32 x qy cells; at qy = 2 every site
+    borders a cell edge):
     the distribution of outcomes -- which sites changed and to what -- over
     20,000 replicas of the register-resident binary32 window and of the
     binary64 window (the oracle's arithmetic) agree by a two-sample
@@ -82,12 +120,12 @@ def test_zgb32_single_window_outcomes_match_binary64(colour):
     from collections import Counter
 
     from scipy.stats import chi2_contingency
-    lx, ly, n = 64, 4, 20000
-    snap = random_lattice(lx, ly, 3, 99 + colour, p=[0.5, 0.25, 0.25])
+    lx, ly, n = 64, 2 * qy, 20000
+    snap = random_lattice(lx, ly, 3, 99 + colour + qy, p=[0.5, 0.25, 0.25])
     reps = [dict(lx=lx, ly=ly, rates=RATES)] * n
     counts = []
     for clock in ("FP32", "FP64"):
-        with F.Context(model="ZGB", q=(32, 2), batch=reps) as b:
+        with F.Context(model="ZGB", q=(32, qy), batch=reps) as b:
             b.set_clock(clock)
             for r in range(n):
                 b.set_state(snap, r)
