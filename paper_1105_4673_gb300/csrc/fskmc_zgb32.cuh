@@ -269,17 +269,26 @@ __device__ uint32_t zgb32_window(uint8_t *wsm, const Replica &R, const CellGeom 
         if (lane == owner) {
             int r = (int)j - (incl - c);
             int kind, x;
+            uint32_t msk;
             if (k == 0 || k == 3) {
                 kind = 0;
-                x = select_bit(k == 0 ? e : a, r);
+                msk = k == 0 ? e : a;
             } else {
+                // the lane's members in order: horizontal bonds, vertical
+                // bonds, the left cross bond, the top-halo bonds; one select
+                // in the mask that holds member r
                 const ZgbBonds B = zgb_bonds(k, row, last, first, ew, e, a, eB, aB, eH, aH, hle, hla, hre, hra);
                 const int ph = __popc(B.H), pv = __popc(B.V);
-                if (r < ph) { kind = 1; x = select_bit(B.H, r); }
-                else if (r < ph + pv) { kind = 2; x = select_bit(B.V, r - ph); }
-                else if (r < ph + pv + (int)B.L) { kind = 3; x = 0; }
-                else { kind = 4; x = select_bit(B.N, r - ph - pv - (int)B.L); }
+                msk = B.H; kind = 1;
+                if (r >= ph) {
+                    r -= ph; msk = B.V; kind = 2;
+                    if (r >= pv) {
+                        r -= pv; msk = B.L; kind = 3;
+                        if (r >= (int)B.L) { r -= (int)B.L; msk = B.N; kind = 4; }
+                    }
+                }
             }
+            x = select_bit(msk, r);
             code = kind * 32 + x;
         }
         code = __shfl_sync(FULLW, code, owner);

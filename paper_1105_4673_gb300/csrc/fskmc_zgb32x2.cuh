@@ -32,21 +32,20 @@ namespace fskmc {
 
 namespace {
 
-// shfl.sync.down by one lane within 16-lane segments, as a volatile asm so
-// that a second fetch of an unchanged value is not merged with the first
-// (which would hold it in a register across the event).
-__device__ __forceinline__ uint32_t shfl_down16_v(uint32_t v)
-{
-    uint32_t r;
-    asm volatile("shfl.sync.down.b32 %0, %1, 1, 0x101f, 0xffffffff;" : "=r"(r) : "r"(v));
-    return r;
-}
-
 // Shared memory one half-warp's cell needs: the staged box rows and the
 // per-window constants.
 __host__ __device__ constexpr int zgbp_half_smem(int qy)
 {
     return 64 * (qy + 2) + (int)sizeof(Zgb32Const);
+}
+
+// Shared memory per warp: both halves' cells, then each lane's bond masks of
+// the two pair classes as counted in the current event ({H0, H1, V0, V1}
+// and {L, N} per class and lane), which the owner of the drawn member reads
+// back instead of recomputing them.
+__host__ __device__ constexpr int zgbp_warp_smem(int qy)
+{
+    return 2 * zgbp_half_smem(qy) + 2 * 32 * 16 + 2 * 32 * 8;
 }
 
 // Two cells per warp: rows of even count 4 <= qy <= 32.
@@ -111,7 +110,7 @@ __device__ __forceinline__ int zgbp_bond_count(const ZgbPairBonds &B)
 // The windows of two cells (qx == 32, even 4 <= qy <= 32) by one warp: half
 // h runs the cell at `at` (its own; `valid` false for a half without a
 // cell) of replica R in the byte lattice src (== dst: ZGB updates in
-// place). wsm: 2 * zgbp_half_smem(qy) bytes of 16-byte aligned shared
+// place). wsm: zgbp_warp_smem(qy) bytes of 16-byte aligned shared
 // memory. Returns this half's events; *bad_out is set if a rank search found
 // no member (never, unless the counts and masks disagree) or a window ran
 // away.
@@ -127,6 +126,8 @@ __device__ uint32_t zgb32x2_window(uint8_t *wsm, const Replica &R, const CellGeo
     const bool ew = colour == 0;
     const bool row = valid && l < (qy >> 1), first = l == 0, last = l == (qy >> 1) - 1;
     uint8_t *raw = wsm + (seg ? zgbp_half_smem(qy) : 0);
+    uint4 *bq = reinterpret_cast<uint4 *>(wsm + 2 * zgbp_half_smem(qy));     // [class - 1][lane]
+    uint2 *bln = reinterpret_cast<uint2 *>(wsm + 2 * zgbp_half_smem(qy) + 1024);
 
     // Stage each half's box rows (the rows above and below its cell too) as
     // four aligned 16-byte chunks: the 16 sites left of the cell, its 32, the
@@ -191,8 +192,16 @@ __device__ uint32_t zgb32x2_window(uint8_t *wsm, const Replica &R, const CellGeo
         int cl[4];
         cl[0] = __popc(e0) + __popc(e1);
         cl[3] = __popc(a0) + __popc(a1);
-        cl[1] = zgbp_bond_count(zgbp_bonds(1, last, first, ew, e0, a0, e1, a1, eB, aB, eH, aH, hl, hr));
-        cl[2] = zgbp_bond_count(zgbp_bonds(2, last, first, ew, e0, a0, e1, a1, eB, aB, eH, aH, hl, hr));
+        {
+            const ZgbPairBonds B1 = zgbp_bonds(1, last, first, ew, e0, a0, e1, a1, eB, aB, eH, aH, hl, hr);
+            const ZgbPairBonds B2 = zgbp_bonds(2, last, first, ew, e0, a0, e1, a1, eB, aB, eH, aH, hl, hr);
+            cl[1] = zgbp_bond_count(B1);
+            cl[2] = zgbp_bond_count(B2);
+            bq[lane] = make_uint4(B1.H0, B1.H1, B1.V0, B1.V1);
+            bq[32 + lane] = make_uint4(B2.H0, B2.H1, B2.V0, B2.V1);
+            bln[lane] = make_uint2(B1.L, B1.N);
+            bln[32 + lane] = make_uint2(B2.L, B2.N);
+        }
         uint32_t n[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) n[k] = __reduce_add_sync(hmask, (uint32_t)cl[k]);
@@ -240,38 +249,50 @@ __device__ uint32_t zgb32x2_window(uint8_t *wsm, const Replica &R, const CellGeo
             live = false;
         }
         const int owner = hit ? __ffs(hit) - 1 : 0;
-        // (the row below fetched again rather than held across the scan)
-        uint32_t eD = shfl_down16_v(e0), aD = shfl_down16_v(a0);
-        if (last) { eD = eH; aD = aH; }
         // kind: 0 site, 1 horizontal bond, 2 vertical bond within the lane,
         // 3 vertical bond below it, 4 left cross bond, 5 top-halo bond; rr:
         // which of the lane's two rows (kinds 0, 1, 4)
         int code = 0;
         if (live && l == owner) {
             int r = (int)j - (incl - c);
-            int kind, x, rr = 0;
+            uint32_t msk;
+            int kind, rr;
             if (k == 0 || k == 3) {
                 const uint32_t m0 = k == 0 ? e0 : a0, m1 = k == 0 ? e1 : a1;
                 const int p0 = __popc(m0);
                 kind = 0;
-                rr = r < p0 ? 0 : 1;
-                x = select_bit(rr ? m1 : m0, rr ? r - p0 : r);
+                rr = r >= p0 ? 1 : 0;
+                msk = rr ? m1 : m0;
+                r -= rr ? p0 : 0;
             } else {
-                const ZgbPairBonds B = zgbp_bonds(k, last, first, ew, e0, a0, e1, a1, eD, aD, eH, aH, hl, hr);
-                // row 2l's members (its horizontal bonds, the vertical bonds
-                // below it, its left cross bond, the top-halo bonds), then row
-                // 2l + 1's: the one-row window's numbering row by row
-                const int pH0 = __popc(B.H0), pV0 = __popc(B.V0), pL0 = (int)(B.L & 1u), pN = __popc(B.N);
-                const int pH1 = __popc(B.H1), pV1 = __popc(B.V1);
-                if (r < pH0) { kind = 1; x = select_bit(B.H0, r); }
-                else if ((r -= pH0) < pV0) { kind = 2; x = select_bit(B.V0, r); }
-                else if ((r -= pV0) < pL0) { kind = 4; x = 0; }
-                else if ((r -= pL0) < pN) { kind = 5; x = select_bit(B.N, r); }
-                else if ((r -= pN) < pH1) { kind = 1; rr = 1; x = select_bit(B.H1, r); }
-                else if ((r -= pH1) < pV1) { kind = 3; x = select_bit(B.V1, r); }
-                else { kind = 4; x = 0; rr = 1; }
+                // this lane's members of class k as counted above: row 2l's
+                // (its horizontal bonds, the vertical bonds below it, its left
+                // cross bond, the top-halo bonds), then row 2l + 1's -- the
+                // one-row window's numbering row by row
+                const uint4 q = bq[(k - 1) * 32 + lane];
+                const uint2 ln = bln[(k - 1) * 32 + lane];
+                const uint32_t L0 = ln.x & 1u, L1 = (ln.x >> 1) & 1u;
+                const int cH0 = __popc(q.x), cV0 = __popc(q.z), cN = __popc(ln.y), cH1 = __popc(q.y);
+                const int cV1 = __popc(q.w);
+                msk = q.x; kind = 1; rr = 0;
+                if (r >= cH0) {
+                    r -= cH0; msk = q.z; kind = 2;
+                    if (r >= cV0) {
+                        r -= cV0; msk = L0; kind = 4;
+                        if (r >= (int)L0) {
+                            r -= (int)L0; msk = ln.y; kind = 5;
+                            if (r >= cN) {
+                                r -= cN; msk = q.y; kind = 1; rr = 1;
+                                if (r >= cH1) {
+                                    r -= cH1; msk = q.w; kind = 3;
+                                    if (r >= cV1) { r -= cV1; msk = L1; kind = 4; }
+                                }
+                            }
+                        }
+                    }
+                }
             }
-            code = (kind << 6) | (rr << 5) | x;
+            code = (kind << 6) | (rr << 5) | select_bit(msk, r);
         }
         code = __shfl_sync(FULLW, code, owner, 16);
         if (live) {

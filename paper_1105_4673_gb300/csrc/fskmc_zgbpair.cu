@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256, 4) fs_zgbp_persistent_kernel(const __grid
 
 size_t zgb_pair_smem_per_warp(int qy)
 {
-    return 2 * (size_t)zgbp_half_smem(qy);
+    return (size_t)zgbp_warp_smem(qy);
 }
 
 bool zgb_pair_shape(int qx, int qy)
