@@ -38,14 +38,10 @@ namespace fskmc {
 
 namespace {
 
-// 4 sites (bytes of v) equal to the byte of st4 -> 4 bits (bit k = byte k).
-__device__ __forceinline__ uint32_t zgb_nibble(uint32_t v, uint32_t st4)
-{
-    const uint32_t t = (__vcmpeq4(v, st4) & 0x80808080u) >> 7;  // bits 0, 8, 16, 24
-    return (t * 0x00204081u) >> 21 & 0xFu;
-}
-
-// Masks of the 32 sites at p (16-byte aligned) in states 0 (empty) and 1 (A).
+// Masks of the 32 sites at p (16-byte aligned) in states 0 (empty) and 1 (A),
+// from bytes holding 0, 1 or 2: a byte's bit 0 marks A, neither of its low
+// two bits empty; one multiply gathers the four flags of a word (bit 8k to
+// bit 21 + k, no carries between them) into a nibble.
 __device__ __forceinline__ void zgb_row_masks(const uint8_t *p, uint32_t &e, uint32_t &a)
 {
     const uint4 u0 = *reinterpret_cast<const uint4 *>(p), u1 = *reinterpret_cast<const uint4 *>(p + 16);
@@ -54,8 +50,10 @@ __device__ __forceinline__ void zgb_row_masks(const uint8_t *p, uint32_t &e, uin
     a = 0u;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        e |= zgb_nibble(v[k], 0u) << (4 * k);
-        a |= zgb_nibble(v[k], 0x01010101u) << (4 * k);
+        const uint32_t ta = v[k] & 0x01010101u;                       // bit 0 of each byte: A
+        const uint32_t te = ~(v[k] | (v[k] >> 1)) & 0x01010101u;      // neither bit: empty
+        e |= ((te * 0x00204081u) >> 21 & 0xFu) << (4 * k);
+        a |= ((ta * 0x00204081u) >> 21 & 0xFu) << (4 * k);
     }
 }
 

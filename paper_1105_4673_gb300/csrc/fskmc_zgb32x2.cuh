@@ -203,8 +203,11 @@ __device__ uint32_t zgb32x2_window(uint8_t *wsm, const Replica &R, const CellGeo
             bln[32 + lane] = make_uint2(B2.L, B2.N);
         }
         uint32_t n[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) n[k] = __reduce_add_sync(hmask, (uint32_t)cl[k]);
+        {  // the four totals as two packed sums (each below 2^16)
+            const uint32_t s03 = __reduce_add_sync(hmask, (uint32_t)cl[0] | ((uint32_t)cl[3] << 16));
+            const uint32_t s12 = __reduce_add_sync(hmask, (uint32_t)cl[1] | ((uint32_t)cl[2] << 16));
+            n[0] = s03 & 0xFFFFu; n[3] = s03 >> 16; n[1] = s12 & 0xFFFFu; n[2] = s12 >> 16;
+        }
         const uint64_t P0 = (uint64_t)n[0] * C.rq[0], P1 = P0 + (uint64_t)n[1] * C.rq[1];
         const uint64_t P2 = P1 + (uint64_t)n[2] * C.rq[2], lami = P2 + (uint64_t)n[3] * C.rq[3];
         if (lami == 0ull) live = false;
@@ -235,6 +238,7 @@ __device__ uint32_t zgb32x2_window(uint8_t *wsm, const Replica &R, const CellGeo
             if (end >= C.hf) live = false;
             else tauf = end;
         }
+        if (!__any_sync(FULLW, live)) break;  // both windows ended at this draw
         // the owner of member j: a prefix scan of the half's counts, then the
         // bit in the owner's masks
         int incl = c;
