@@ -187,11 +187,11 @@ def algo_lane_ops_per_event(model, q, fp64):
 # source they were taken on: DRAM bytes per fractional window of the
 # workload and the issue-slot utilisation.
 PROFILED = {
-    ("fs_persistent_kernel<ZGB,float,rows in registers>", "zgb16384"): {
-        "src": ["fskmc_window.cu", "fskmc_zgb32.cuh", "fskmc_device.cuh", "fskmc_internal.h",
-                "fskmc_persistent.h", "philox.cuh"],
-        "dram_bytes_per_window": 510047949, "issue_active": 0.728,
-        "src_sha256": "e54b881972defb6ddeb78b0ce1c7408a2667772bf262140407fb8eccdb856bba"},
+    ("fs_zgbp_persistent_kernel", "zgb16384"): {
+        "src": ["fskmc_zgbpair.cu", "fskmc_zgb32x2.cuh", "fskmc_zgb32.cuh", "fskmc_device.cuh", "fskmc_internal.h",
+                "philox.cuh"],
+        "dram_bytes_per_window": 498167526, "issue_active": 0.767,
+        "src_sha256": "af5a7c38ea3ba1bee271006506458729f47ae0eb8227d82abecfd391ed845805"},
 }
 
 
