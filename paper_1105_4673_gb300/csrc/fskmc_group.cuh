@@ -39,11 +39,13 @@ constexpr unsigned FULL = 0xffffffffu;
 // Per-cell shared memory: the cell and its halo (one byte per site), the
 // class code of every own site, KS x W membership words (word l of class k
 // holds sites 32l .. 32l+31, owned by lane l), 16 class counts, the counts
-// as binary64. Cells are spaced a multiple of 128 bytes plus W words apart,
-// so the cells' words at the same offset fall in different banks.
+// as binary64, and per box row three bit words (the row's cell sites, its
+// left and its right halo site; 16-wide cells of a byte lattice). Cells are
+// spaced a multiple of 128 bytes plus W words apart, so the cells' words at
+// the same offset fall in different banks.
 struct GLayout {
     int BW, BH, nsite;
-    int scls_off, mask_off, cnt_off, dcnt_off;
+    int scls_off, mask_off, cnt_off, dcnt_off, rowb_off;
     int stride;
 };
 
@@ -64,6 +66,8 @@ __host__ __device__ inline GLayout make_glayout(int qx, int qy, int W)
     o += 4 * MAX_CLASSES;
     L.dcnt_off = o;
     o += 8 * MAX_CLASSES;
+    L.rowb_off = o;
+    o += 12 * L.BH;
     L.stride = ((o + 127) & ~127) + 4 * W;
     return L;
 }
@@ -102,6 +106,7 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     uint32_t *mask = reinterpret_cast<uint32_t *>(csm + Lo.mask_off);
     int *cnt = reinterpret_cast<int *>(csm + Lo.cnt_off);
     double *dcnt = reinterpret_cast<double *>(csm + Lo.dcnt_off);
+    uint32_t *rowb = reinterpret_cast<uint32_t *>(csm + Lo.rowb_off);  // [box row][cell, left, right]
 
     const int lx = at.lx, ly = at.ly;
     const uint32_t m = at.m;
@@ -110,6 +115,9 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     // Stage the cell and its halo (periodic wrap) from the window-start
     // state; on the ring only the cell's own row.
     const bool rows16 = !PACKED && (qx & 15) == 0 && (lx & 15) == 0 && (X0 & 15) == 0;
+    // 16-wide cells of a byte lattice in 2D: the staging also records every
+    // box row as bits, and the class build works on whole rows of bits
+    const bool rowbits = rows16 && !ring && qx == 16;
     if (valid && rows16) {
         // byte lattice, cell width a multiple of 16: each box row is qx/16
         // aligned 16-byte chunks of the cell's row plus its two halo sites;
@@ -122,11 +130,12 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
         while (c >= per_row) { c -= per_row; ++by; }
         for (int i0 = gl; i0 < total; i0 += UB16 * W) {
             uint4 v[UB16];
-            int bi[UB16], kind[UB16];
+            int bi[UB16], kind[UB16], rw[UB16];
 #pragma unroll
             for (int u = 0; u < UB16; ++u) {
                 kind[u] = -1;  // -1 none, 0 chunk, 1 halo site
                 bi[u] = 0;
+                rw[u] = 3 * by + (c < nch ? 0 : (c == nch ? 1 : 2));
                 v[u] = make_uint4(0u, 0u, 0u, 0u);
                 if (i0 + u * W < total) {
                     int gy = Y0 - HW + by;
@@ -154,8 +163,18 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
                     const uint32_t wv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                     for (int b = 0; b < 16; ++b) box[bi[u] + b] = (uint8_t)(wv[b >> 2] >> (8 * (b & 3)));
+                    if (rowbits) {
+                        // the chunk's 16 sites (states 0/1) as bits 1..16 of the
+                        // box row: one multiply gathers a word's four bytes
+                        uint32_t m16 = 0u;
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4)
+                            m16 |= ((((wv[q4] & 0x01010101u) * 0x00204081u) >> 21) & 0xFu) << (4 * q4);
+                        rowb[rw[u]] = m16 << HW;
+                    }
                 } else if (kind[u] == 1) {
                     box[bi[u]] = (uint8_t)v[u].x;
+                    if (rowbits) rowb[rw[u]] = (v[u].x & 1u) << (rw[u] % 3 == 1 ? 0 : HW + qx);
                 }
             }
         }
@@ -205,7 +224,57 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
     // states are 0/1, so n is the sum of the neighbours' bytes); the lane
     // gathers sigma and the three bits of n as bit planes over its sites and
     // forms each class's membership word from them.
-    if (valid) {
+    if (valid && rowbits) {
+        // lane gl's word holds cell rows 2 gl and 2 gl + 1: their states and
+        // the bit-sliced count of their occupied neighbours from box rows
+        // 2 gl .. 2 gl + 3 (rows past the box are empty; their sites lie
+        // past the cell and are masked off)
+        uint32_t ps = 0u, p0 = 0u, p1 = 0u, p2 = 0u;
+        const int i0 = gl * 32;
+        const int nt = min(32, nsite - i0);
+        if (nt > 0) {
+            uint32_t rb[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int b = 2 * gl + r;
+                rb[r] = b < BH ? (rowb[3 * b] | rowb[3 * b + 1] | rowb[3 * b + 2]) : 0u;
+            }
+            uint32_t sN = 0u, sS = 0u, sW = 0u, sE = 0u;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                ps |= ((rb[r + 1] >> 1) & 0xFFFFu) << (16 * r);
+                sN |= ((rb[r] >> 1) & 0xFFFFu) << (16 * r);
+                sS |= ((rb[r + 2] >> 1) & 0xFFFFu) << (16 * r);
+                sW |= (rb[r + 1] & 0xFFFFu) << (16 * r);
+                sE |= ((rb[r + 1] >> 2) & 0xFFFFu) << (16 * r);
+            }
+            // n = N + S + W + E, bit by bit: two half adders, then the carries
+            const uint32_t a1 = sN ^ sS, c1 = sN & sS, a2 = sW ^ sE, c2 = sW & sE;
+            const uint32_t c3 = a1 & a2;
+            p0 = a1 ^ a2;
+            p1 = c1 ^ c2 ^ c3;
+            p2 = c1 & c2;
+            // the class bytes, four sites per store: SK sigma + n
+#pragma unroll
+            for (int t4 = 0; t4 < 8; ++t4) {
+                if (4 * t4 < nt) {
+                    const auto e4 = [t4](uint32_t x) { return (((x >> (4 * t4)) & 0xFu) * 0x00204081u) & 0x01010101u; };
+                    *reinterpret_cast<uint32_t *>(scls + i0 + 4 * t4) =
+                        (uint32_t)SK * e4(ps) + e4(p0) + 2u * e4(p1) + 4u * e4(p2);
+                }
+            }
+        }
+        const uint32_t vm = nt >= 32 ? 0xffffffffu : (nt > 0 ? (1u << nt) - 1u : 0u);
+#pragma unroll
+        for (int kk = 0; kk < TR::KS; ++kk) {
+            const int sg = kk / SK, v = kk % SK;
+            uint32_t mk = vm & (sg ? ps : ~ps);
+            mk &= (v & 1) ? p0 : ~p0;
+            mk &= (v & 2) ? p1 : ~p1;
+            mk &= (v & 4) ? p2 : ~p2;
+            mask[kk * W + gl] = mk;
+        }
+    } else if (valid) {
         uint32_t ps = 0u, p0 = 0u, p1 = 0u, p2 = 0u;
         const int i0 = gl * 32;
         const int nt = min(32, nsite - i0);  // sites of this word (none past the cell's last)
