@@ -28,6 +28,7 @@
 
 #include "fskmc_cell.cuh"
 #include "fskmc_device.cuh"
+#include "fskmc_diff32.cuh"
 #include "fskmc_zgb32.cuh"
 #include "fskmc_internal.h"
 #include "fskmc_persistent.h"
@@ -38,8 +39,9 @@ namespace fskmc {
 namespace {
 
 // Plain engine: one launch per window, one warp per active cell of one replica.
-// ROWREG: 32-wide ZGB cells with the binary32 clock, held in registers
-// (zgb32_window); otherwise the generic window (cell_window).
+// ROWREG: 32-wide ZGB or diffusion cells with the binary32 clock, held in
+// registers (zgb32_window, diff32_window); otherwise the generic window
+// (cell_window).
 // Held to 64 registers (two 512-thread blocks per SM): with more warps
 // resident the latency of one event's chain hides better (16384^2 ZGB:
 // +2-8%; the binary64 forms spill a few words and still gain).
@@ -74,7 +76,10 @@ __global__ void __launch_bounds__(512, 2) fs_window_kernel(WindowArgs a, int nac
     bool amb = false, bad = false;
     uint32_t nexact = 0;
     uint32_t e;
-    if constexpr (ROWREG)
+    if constexpr (ROWREG && MODEL == DIFFUSION)
+        e = diff32_window<false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cell_at(R, a.geom, cx, cy),
+                                 a.colour, a.w, a.h, a.seed, src, dst, lane, &bad);
+    else if constexpr (ROWREG)
         e = zgb32_window<false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cell_at(R, a.geom, cx, cy),
                                 a.colour, a.w, a.h, a.seed, src, dst, lane, &bad);
     else
@@ -204,7 +209,10 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
             bool amb = false, bad = false;
             uint32_t nexact = 0;
             uint32_t e;
-            if constexpr (ROWREG)
+            if constexpr (ROWREG && MODEL == DIFFUSION)
+                e = diff32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
+                                        P.h[i], P.seed, cur, nxt, lane, &bad);
+            else if constexpr (ROWREG)
                 e = zgb32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
                                        P.h[i], P.seed, cur, nxt, lane, &bad);
             else
@@ -251,6 +259,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     }
     int spw = make_layout<MODEL>(a.geom.qx, a.geom.qy).bytes;
     if constexpr (MODEL == ZGB) spw = std::max(spw, zgb32_smem(a.geom.qy));  // either window fits
+    if constexpr (MODEL == DIFFUSION) spw = std::max(spw, diff32_smem(a.geom.qy));
     size_t smem = (size_t)spw * wpb;
     int blocks = (nactive + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
@@ -258,7 +267,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
     if constexpr (is_spin_flip<MODEL>()) {
         if (a.packed) kern = fp32 ? fs_window_kernel<MODEL, float, true> : fs_window_kernel<MODEL, double, true>;
     }
-    if constexpr (MODEL == ZGB) {
+    if constexpr (MODEL == ZGB || MODEL == DIFFUSION) {
         if (fp32 && a.geom.qx == 32 && a.geom.qy >= 2) kern = fs_window_kernel<MODEL, float, false, true>;
     }
     if (!kern) kern = fp32 ? fs_window_kernel<MODEL, float, false> : fs_window_kernel<MODEL, double, false>;
@@ -270,7 +279,7 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
 template <int MODEL>
 void *persistent_kernel_ptr(int fp32, bool packed, int qx, int qy)
 {
-    if constexpr (MODEL == ZGB) {
+    if constexpr (MODEL == ZGB || MODEL == DIFFUSION) {
         if (fp32 && qx == 32 && qy >= 2) return (void *)fs_persistent_kernel<MODEL, float, false, true>;
     }
     if constexpr (is_spin_flip<MODEL>()) {
@@ -301,7 +310,7 @@ size_t window_smem_per_warp(int model, int qx, int qy)
     switch (model) {
     case ADSDES: return make_layout<ADSDES>(qx, qy).bytes;
     case ISING: return make_layout<ISING>(qx, qy).bytes;
-    case DIFFUSION: return make_layout<DIFFUSION>(qx, qy).bytes;
+    case DIFFUSION: return std::max(make_layout<DIFFUSION>(qx, qy).bytes, diff32_smem(qy));
     case ZGB: return std::max(make_layout<ZGB>(qx, qy).bytes, zgb32_smem(qy));
     case ISING1D: return make_layout<ISING1D>(qx, qy).bytes;
     }
