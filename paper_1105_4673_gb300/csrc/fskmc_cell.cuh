@@ -104,6 +104,32 @@ __device__ void copy_unwritten(const uint8_t *src, uint8_t *dst, int lx, int ly,
                                int cx, int cy, int col, int lane)
 {
     const int X0 = cx * qx, Y0 = cy * qy;
+    if (qx == 32 && (lx & 31) == 0) {
+        // 32-wide cells: one 32-byte row per lane (32-byte aligned), read as
+        // two 16-byte words; E windows write its bytes 1..30 as aligned
+        // 1-, 2-, 4- and 8-byte pieces, O windows rows 1..qy-2 whole
+        const int r0 = col == 0 ? 0 : 1, r1 = col == 0 ? qy : qy - 1;
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const int64_t o = (int64_t)(Y0 + r) * lx + X0;
+            const uint4 *sp = reinterpret_cast<const uint4 *>(src + o);
+            const uint4 a = PERSIST ? __ldcg(sp) : sp[0], b = PERSIST ? __ldcg(sp + 1) : sp[1];
+            uint8_t *d = dst + o;
+            if (col == 0) {
+                d[1] = (uint8_t)(a.x >> 8);
+                *reinterpret_cast<uint16_t *>(d + 2) = (uint16_t)(a.x >> 16);
+                *reinterpret_cast<uint32_t *>(d + 4) = a.y;
+                *reinterpret_cast<uint2 *>(d + 8) = make_uint2(a.z, a.w);
+                *reinterpret_cast<uint2 *>(d + 16) = make_uint2(b.x, b.y);
+                *reinterpret_cast<uint32_t *>(d + 24) = b.z;
+                *reinterpret_cast<uint16_t *>(d + 28) = (uint16_t)b.w;
+                d[30] = (uint8_t)(b.w >> 16);
+            } else {
+                reinterpret_cast<uint4 *>(d)[0] = a;
+                reinterpret_cast<uint4 *>(d)[1] = b;
+            }
+        }
+        return;
+    }
     const int c0 = col == 0 ? 1 : 0, wdt = col == 0 ? qx - 2 : qx;  // columns c0 .. c0 + wdt - 1
     const int r0 = col == 0 ? 0 : 1, nrow = col == 0 ? qy : qy - 2;  // rows r0 .. r0 + nrow - 1
     if (wdt <= 0 || nrow <= 0) return;
