@@ -410,20 +410,26 @@ __device__ void group_window(uint8_t *csm, const GLayout &Lo, const Replica &R, 
             if (dbits(lamd) == 0) act = false;
         } else {
             // exact integer prefix sums in class order: a width-W scan per
-            // class slot, then the slots' running bases
+            // class slot (over the slot's nc classes only: its last slot may
+            // hold fewer than W), then the slots' running bases
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
                 const int k = gl + W * s;
+                constexpr int nc_last = K - W * (CPL - 1);
+                const int nc = s < CPL - 1 ? W : nc_last;
                 P[s] = (uint64_t)(k < K ? (uint32_t)cnt[k] : 0u) * rq[s];
 #pragma unroll
                 for (int off = 1; off < W; off <<= 1) {
-                    const uint64_t v = __shfl_up_sync(FULL, P[s], off, W);
-                    if (gl >= off) P[s] += v;
+                    if (off < nc) {
+                        const uint64_t v = __shfl_up_sync(FULL, P[s], off, W);
+                        if (gl >= off) P[s] += v;
+                    }
                 }
             }
 #pragma unroll
             for (int s = 0; s < CPL; ++s) {
-                const uint64_t tot = __shfl_sync(FULL, P[s], W - 1, W);
+                const int nc = s < CPL - 1 ? W : K - W * (CPL - 1);
+                const uint64_t tot = __shfl_sync(FULL, P[s], nc - 1, W);
                 P[s] += lami;
                 lami += tot;
             }
