@@ -411,10 +411,14 @@ constexpr int ORDER_GROUP = 1024;
 int lanes_per_cell(const fskmc_ctx *c)
 {
     if (c->grouping == 0) return 32;
-    // ZGB, 32-wide cells of an even number of rows, binary32 clock: two
-    // cells per warp, 16 lanes each (fskmc_zgbpair.cu)
-    if (c->model == FSKMC_ZGB)
-        return (c->clock == FSKMC_CLOCK_FP32 && fskmc::zgb_pair_shape(c->qx, c->qy)) ? 16 : 32;
+    // ZGB, 32-wide cells, binary32 clock: four cells per warp (8 lanes each,
+    // rows a multiple of 4 from 8; fskmc_zgbquad.cu), else two (16 lanes,
+    // an even number of rows; fskmc_zgbpair.cu)
+    if (c->model == FSKMC_ZGB) {
+        if (c->clock != FSKMC_CLOCK_FP32) return 32;
+        if (fskmc::zgb_quad_shape(c->qx, c->qy)) return 8;  // four cells per warp, 8 lanes each
+        return fskmc::zgb_pair_shape(c->qx, c->qy) ? 16 : 32;
+    }
     const int W = fskmc::group_width(c->model, c->qx, c->qy);
     return W >= 32 ? 32 : W;
 }
@@ -695,7 +699,9 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *c, int32_t warps)
     if (warps < 1 || warps > 16) return fail(c, FSKMC_EINVAL, "warps per block must be 1..16");
     size_t need = std::max({fskmc::window_smem_per_warp(c->model, c->qx, c->qy),
                             fskmc::group_smem_per_warp(c->model, c->qx, c->qy),
-                            c->model == FSKMC_ZGB ? fskmc::zgb_pair_smem_per_warp(c->qy) : (size_t)0}) *
+                            c->model == FSKMC_ZGB ? std::max(fskmc::zgb_pair_smem_per_warp(c->qy),
+                                                             fskmc::zgb_quad_smem_per_warp())
+                                                  : (size_t)0}) *
                   (size_t)warps;
     if (need > 200 * 1024) return fail(c, FSKMC_EINVAL, "%d warps need %zu B of shared memory", warps, need);
     c->wpb = warps;

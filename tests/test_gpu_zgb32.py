@@ -1,6 +1,7 @@
 """The register-resident binary32 windows of 32-wide ZGB cells (the batched
-form of the 16384^2 benchmark) -- one cell per warp, or two cells per warp
-at two rows per lane -- against the binary64 form, which is the oracle's
+form of the 16384^2 benchmark) -- one cell per warp, two cells per warp at
+two rows per lane, or four at four rows per lane -- against the binary64
+form, which is the oracle's
 arithmetic bit for bit: pair events on undirected bonds at twice the
 directed rate are the same process, so over many replicas from the same
 snapshot the event counts and every observable agree within 4 standard
@@ -63,11 +64,12 @@ def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T
 
 @pytest.mark.parametrize("lx,ly,qy,scheme", [
     (128, 128, 32, "STRANG"), (256, 64, 16, "RANDOM"), (64, 96, 6, "LIE"), (128, 48, 4, "STRANG"),
-    (64, 64, 2, "LIE"),
+    (64, 64, 2, "LIE"), (192, 64, 8, "STRANG"), (128, 96, 12, "RANDOM"),
 ])
 def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
-    """Plain and persistent engines, one and two cells per warp: the same
-    lattice, event count and per-cell workloads in all four."""
+    """Plain and persistent engines, one cell per warp and several (four for
+    rows a multiple of 4 from 8, else two for an even number of rows): the
+    same lattice, event count and per-cell workloads in all four."""
     snap = random_lattice(lx, ly, 3, 7 + qy, p=[0.6, 0.2, 0.2])
     out = []
     for engine in ("PLAIN", "PERSISTENT"):
@@ -76,8 +78,9 @@ def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
                 c.set_clock("FP32")
                 c.set_engine(engine)
                 c.set_cell_grouping(grouped)
-                pair = grouped and qy % 2 == 0 and qy >= 4
-                assert c.info()["lanes_per_cell"] == (16 if pair else 32)
+                quad = grouped and qy % 4 == 0 and qy >= 8
+                pair = grouped and not quad and qy % 2 == 0 and qy >= 4
+                assert c.info()["lanes_per_cell"] == (8 if quad else (16 if pair else 32))
                 c.set_state(snap)
                 c.run(scheme, 0.02, 0.4, 5)
                 st = c.stats()
@@ -87,14 +90,16 @@ def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
         assert np.array_equal(g, out[0][0]) and ev == out[0][1] > 0 and np.array_equal(wl, out[0][2])
 
 
-def test_zgb32_two_cells_per_warp_batch_equals_one_cell():
+@pytest.mark.parametrize("qy", [16, 8])  # four cells per warp; 64-row replicas hold (32, 8) cells too
+def test_zgb32_several_cells_per_warp_batch_equals_one_cell(qy):
     """A batch of replicas of different sizes and rates in the persistent
-    engine: two cells per warp equals one cell per warp, replica by replica."""
+    engine: several cells per warp equal one cell per warp, replica by
+    replica."""
     reps = [dict(lx=64, ly=64, rates=RATES), dict(lx=128, ly=64, rates=dict(yA=0.45, kr=20.0, kd=0.1)),
             dict(lx=64, ly=128, rates=dict(yA=0.6, kr=5.0, kd=0.0))]
     res = []
     for grouped in (True, False):
-        with F.Context(model="ZGB", q=(32, 16), batch=reps) as b:
+        with F.Context(model="ZGB", q=(32, qy), batch=reps) as b:
             b.set_clock("FP32")
             b.set_engine("PERSISTENT")
             b.set_cell_grouping(grouped)
@@ -107,7 +112,7 @@ def test_zgb32_two_cells_per_warp_batch_equals_one_cell():
 
 
 @pytest.mark.parametrize("colour", [0, 1])
-@pytest.mark.parametrize("qy", [2, 4])  # one cell per warp; two cells per warp
+@pytest.mark.parametrize("qy", [2, 4, 8])  # one, two and four cells per warp
 def test_zgb32_single_window_outcomes_match_binary64(colour, qy):
     """One short window (about an event per active half-lattice) from a fixed
     snapshot on a 64 x 2qy lattice (32 x qy cells; at qy = 2 every site
