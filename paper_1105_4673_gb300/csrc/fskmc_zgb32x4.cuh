@@ -279,28 +279,31 @@ __device__ uint32_t zgb32x4_window(uint8_t *wsm, const Replica &R, const CellGeo
             if (kind == 0) {
                 if (l == owner) {
                     // A adsorbs on an empty site (class 0) or desorbs (class 3)
+                    const bool toA = k == 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint32_t m = rr == q ? bit : 0u;
-                        if (k == 0) { e[q] &= ~m; a[q] |= m; }
-                        else { a[q] &= ~m; e[q] |= m; }
+                        e[q] = toA ? (e[q] & ~m) : (e[q] | m);
+                        a[q] = toA ? (a[q] | m) : (a[q] & ~m);
                     }
                 }
             } else {
                 // B2 adsorption makes both ends B, the reaction both ends empty
                 const bool toB = k == 1;
-                const uint32_t hm = bit | (x < 31 ? bit << 1 : 0u);
                 const uint32_t hrc = (kind == 1 && x == 31) ? 3u << (2 * rr) : 0u;
                 const uint32_t hlc = kind == 4 ? 3u << (2 * rr) : 0u;
                 const bool hrow = kind == 5 || (kind == 3 && last);
                 const uint32_t hval = toB ? 0u : 0x55u;  // empty: bit 2r of a pair; B: neither
                 if (l == owner) {
+                    // the sites of the member's row rr (both ends of a horizontal
+                    // bond, the site of a cross or top-halo bond, the upper end
+                    // of a vertical one) and, for a vertical bond within the
+                    // lane, of row rr + 1
+                    const uint32_t mA = kind == 1 ? (bit | (x < 31 ? bit << 1 : 0u)) : (kind == 4 ? 1u : bit);
+                    const uint32_t mB = kind == 2 ? bit : 0u;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const uint32_t m = ((kind == 1 && rr == q) ? hm : 0u) |
-                                           ((kind == 2 && (rr == q || rr + 1 == q)) ? bit : 0u) |
-                                           ((kind == 3 && q == 3) ? bit : 0u) | ((kind == 4 && rr == q) ? 1u : 0u) |
-                                           ((kind == 5 && q == 0) ? bit : 0u);
+                        const uint32_t m = (rr == q ? mA : 0u) | (rr + 1 == q ? mB : 0u);
                         e[q] = toB ? (e[q] & ~m) : (e[q] | m);
                         a[q] &= ~m;
                     }
