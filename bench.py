@@ -207,9 +207,11 @@ def src_sha(names):
 def kernel_name(engine, model, fp64, packed, lanes, q=None):
     """The window kernel the bench's configuration launches."""
     grouped = lanes < 32
-    if model == "ZGB" and grouped:  # four (8 lanes each) or two (16) 32-wide cells per warp, binary32
-        tag = "zgbq" if lanes == 8 else "zgbp"
-        return {"PLAIN": f"fs_{tag}_window_kernel", "PERSISTENT": f"fs_{tag}_persistent_kernel"}[engine]
+    if model == "ZGB" and grouped:  # 32 / lanes 32-wide cells per warp, binary32
+        if lanes == 16:
+            return {"PLAIN": "fs_zgbp_window_kernel", "PERSISTENT": "fs_zgbp_persistent_kernel"}[engine]
+        kind = {"PLAIN": "fs_zgbq_window_kernel", "PERSISTENT": "fs_zgbq_persistent_kernel"}[engine]
+        return f"{kind}<{32 // lanes}>"
     base = {("PLAIN", False): "fs_window_kernel", ("PERSISTENT", False): "fs_persistent_kernel",
             ("PLAIN", True): "fs_group_kernel", ("PERSISTENT", True): "fs_group_persistent_kernel"}
     args = [model, "double" if fp64 else "float"] + (["packed"] if packed else [])

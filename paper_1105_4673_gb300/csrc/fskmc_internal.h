@@ -110,12 +110,13 @@ bool zgb_pair_shape(int qx, int qy);
 size_t zgb_pair_smem_per_warp(int qy);
 cudaError_t launch_zgb_pair_window(const WindowArgs &a, int nactive, int wpb, cudaStream_t st);
 void *zgb_pair_persistent_kernel();
-// The four-cells-per-warp ZGB window (fskmc_zgbquad.cu): 32-wide cells of 8
-// to 32 rows in multiples of 4, binary32 clock; as the two-cell calls.
-bool zgb_quad_shape(int qx, int qy);
-size_t zgb_quad_smem_per_warp();
-cudaError_t launch_zgb_quad_window(const WindowArgs &a, int nactive, int wpb, cudaStream_t st);
-void *zgb_quad_persistent_kernel();
+// The rl-cells-per-warp ZGB window (fskmc_zgbquad.cu; rl = 4 or 8): 32-wide
+// cells of 2 rl to 32 rows in multiples of rl, binary32 clock; as the
+// two-cell calls.
+bool zgb_multi_shape(int rl, int qx, int qy);
+size_t zgb_multi_smem_per_warp(int rl);
+cudaError_t launch_zgb_multi_window(int rl, const WindowArgs &a, int nactive, int wpb, cudaStream_t st);
+void *zgb_multi_persistent_kernel(int rl);
 
 // Lanes per cell of the grouped window kernels (several small cells per
 // warp, spin-flip models only): the lanes owning the cell's 32-site words,

@@ -252,8 +252,9 @@ cudaError_t launch_model(int fp32, const WindowArgs &a, int nactive, int wpb, cu
         // ZGB: two 32-wide cells per warp (binary32 clock); the spin-flip
         // models: the grouped kernels
         if constexpr (MODEL == ZGB) {
-            if (fp32 && a.lanes_per_cell == 8 && zgb_quad_shape(a.geom.qx, a.geom.qy))
-                return launch_zgb_quad_window(a, nactive, wpb, st);
+            const int rl = 32 / a.lanes_per_cell;  // cells per warp
+            if (fp32 && (rl == 4 || rl == 8) && zgb_multi_shape(rl, a.geom.qx, a.geom.qy))
+                return launch_zgb_multi_window(rl, a, nactive, wpb, st);
             if (!fp32 || a.lanes_per_cell != 16 || !zgb_pair_shape(a.geom.qx, a.geom.qy)) return cudaErrorInvalidValue;
             return launch_zgb_pair_window(a, nactive, wpb, st);
         }
@@ -476,17 +477,18 @@ cudaError_t persistent_run(PersistentState **pst, const PersistentRun &run, cuda
         // memory
         const bool grouped = run.lanes_per_cell < 32;
         const bool zpair = grouped && run.model == ZGB;
-        const bool zquad = zpair && run.lanes_per_cell == 8;
-        if (zpair && !(run.fp32 && (zquad ? zgb_quad_shape(run.qx, run.qy) : zgb_pair_shape(run.qx, run.qy)))) {
+        const int zrl = 32 / run.lanes_per_cell;  // cells per warp
+        const bool zquad = zpair && (zrl == 4 || zrl == 8);
+        if (zpair && !(run.fp32 && (zquad ? zgb_multi_shape(zrl, run.qx, run.qy) : zgb_pair_shape(run.qx, run.qy)))) {
             *msg = "multi-cell ZGB kernel: binary32 clock, 32-wide cells of a suitable number of rows";
             return cudaErrorInvalidValue;
         }
-        void *kern = zquad     ? zgb_quad_persistent_kernel()
+        void *kern = zquad     ? zgb_multi_persistent_kernel(zrl)
                      : zpair   ? zgb_pair_persistent_kernel()
                      : grouped ? group_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy, true)
                                : persistent_kernel_for(run.model, run.fp32, run.packed, run.qx, run.qy);
         if (!kern) { *msg = "no persistent kernel for this model and cell width"; return cudaErrorInvalidValue; }
-        const int wbytes = zquad     ? (int)zgb_quad_smem_per_warp()
+        const int wbytes = zquad     ? (int)zgb_multi_smem_per_warp(zrl)
                            : zpair   ? (int)zgb_pair_smem_per_warp(run.qy)
                            : grouped ? (int)group_smem_per_warp(run.model, run.qx, run.qy)
                                      : (int)window_smem_per_warp(run.model, run.qx, run.qy);

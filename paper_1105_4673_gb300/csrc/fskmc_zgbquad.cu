@@ -1,12 +1,12 @@
-// Kernels of the four-cells-per-warp ZGB window (fskmc_zgb32x4.cuh): 32-wide
-// cells whose rows are a multiple of 4, from 8 to 32, with the binary32
-// clock.
+// Kernels of the RL-cells-per-warp ZGB window (fskmc_zgb32x4.cuh; RL = 4 or
+// 8): 32-wide cells whose rows are a multiple of RL, from 2 RL to 32, with
+// the binary32 clock.
 //
-// fs_zgbq_window_kernel: one fractional window (Eqs. totalrate and skeleton
-// on every active cell), warp g running the window's active cells 4g ..
-// 4g + 3 (in issue order when one is given).
-// fs_zgbq_persistent_kernel: the persistent engine of fskmc_window.cu for
-// this window, a task being four consecutive active cells of one window;
+// fs_zgbq_window_kernel<RL>: one fractional window (Eqs. totalrate and
+// skeleton on every active cell), warp g running the window's active cells
+// RL g .. RL g + RL - 1 (in issue order when one is given).
+// fs_zgbq_persistent_kernel<RL>: the persistent engine of fskmc_window.cu
+// for this window, a task being RL consecutive active cells of one window;
 // each cell waits on its own prerequisites (its previous active window, its
 // edge neighbours' last active window before this one) with the bounded,
 // backed-off polls of wait_epochs, and publishes its own epoch.
@@ -22,12 +22,14 @@ namespace fskmc {
 
 namespace {
 
-// The events of the warp's four cells to counter 0 and their failures to
-// counter 3 (lane 0; every lane calls it).
+// The events of the warp's RL cells to counter 0 and their failures to
+// counter 3 (lane 0; every lane calls it; W lanes per cell).
+template <int W>
 __device__ __forceinline__ void zgbq_count(unsigned long long *counters, int lane, bool valid, uint32_t e, bool bad)
 {
-    const uint32_t evs = __reduce_add_sync(0xffffffffu, (valid && (lane & 7) == 0) ? e : 0u);
-    const unsigned bads = __ballot_sync(0xffffffffu, bad) & 0x01010101u;
+    constexpr unsigned leads = W == 8 ? 0x01010101u : 0x11111111u;  // lane 0 of every cell
+    const uint32_t evs = __reduce_add_sync(0xffffffffu, (valid && (lane & (W - 1)) == 0) ? e : 0u);
+    const unsigned bads = __ballot_sync(0xffffffffu, bad) & leads;
     if (lane == 0) {
         atomicAdd(&counters[0], (unsigned long long)evs);
         if (bads) atomicAdd(&counters[3], (unsigned long long)__popc(bads));
@@ -35,14 +37,16 @@ __device__ __forceinline__ void zgbq_count(unsigned long long *counters, int lan
 }
 
 // Held to 64 registers (as the other one-window kernels).
+template <int RL>
 __global__ void __launch_bounds__(512, 2) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
+    constexpr int W = 32 / RL;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int g = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (4 * g >= nactive) return;
-    const int cidx = 4 * g + (lane >> 3);
+    if (RL * g >= nactive) return;
+    const int cidx = RL * g + lane / W;
     const bool valid = cidx < nactive;
     const Replica &R = a.reps[a.rep_index];
     int cx = 0, cy = 0;
@@ -58,24 +62,27 @@ __global__ void __launch_bounds__(512, 2) fs_zgbq_window_kernel(WindowArgs a, in
         }
     }
     bool bad = false;
-    const uint32_t e = zgb32x4_window<false>(smem + (size_t)wib * smem_per_warp, R, a.geom,
-                                             cell_at(R, a.geom, cx, cy), valid, a.colour, a.w, a.h, a.seed,
-                                             a.src + R.lat_off, a.dst + R.lat_off, lane, &bad);
-    if ((lane & 7) == 0 && valid) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
-    zgbq_count(a.counters, lane, valid, e, bad);
+    const uint32_t e = zgbm_window<RL, false>(smem + (size_t)wib * smem_per_warp, R, a.geom,
+                                              cell_at(R, a.geom, cx, cy), valid, a.colour, a.w, a.h, a.seed,
+                                              a.src + R.lat_off, a.dst + R.lat_off, lane, &bad);
+    if ((lane & (W - 1)) == 0 && valid) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
+    zgbq_count<W>(a.counters, lane, valid, e, bad);
 }
 
-// Held to 64 registers (four 256-thread blocks per SM).
-__global__ void __launch_bounds__(256, 4) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
+// Held to 64 registers (four 256-thread blocks per SM) with four cells per
+// warp, to 80 (three) with eight, where 64 would spill.
+template <int RL>
+__global__ void __launch_bounds__(256, RL == 8 ? 3 : 4) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
                                                                     int smem_per_warp)
 {
+    constexpr int W = 32 / RL;
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int gl = lane & 7;  // lane within the cell's group
+    const int gl = lane & (W - 1);  // lane within the cell's group
     uint8_t *wsm = smem + (size_t)wib * smem_per_warp;
     const int per_window = P.total_active;
-    const int chunks = (per_window + 3) >> 2;
+    const int chunks = (per_window + RL - 1) / RL;
     const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)chunks;
     for (;;) {
         // the dequeue and the abort flag in one round trip
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(256, 4) fs_zgbq_persistent_kernel(const __grid
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= total || __shfl_sync(0xffffffffu, ab, 0)) break;
         const int i = (int)(t / (unsigned long long)chunks);
-        const int u = 4 * (int)(t % (unsigned long long)chunks) + (lane >> 3);
+        const int u = RL * (int)(t % (unsigned long long)chunks) + lane / W;
         const bool valid = u < per_window;
         int r = 0, k = 0;
         if (valid) {
@@ -112,24 +119,31 @@ __global__ void __launch_bounds__(256, 4) fs_zgbq_persistent_kernel(const __grid
             }
         }
         const int slot = R.cell_off + cy * R.ncx + cx;
-        // epoch[c] = 1 + the last window in which cell c was active. Lane 0
-        // of a group: its cell's previous active window; lanes 1..4: the
-        // edge neighbours' last active window before this one.
+        // epoch[c] = 1 + the last window in which cell c was active.
+        // Dependency 0: the cell's previous active window; 1..4: the edge
+        // neighbours' last active window before this one; lane gl of a group
+        // waits on dependencies gl, gl + W.
         {
             const int2 pv = P.prev[widx];
-            const int ex = gl == 1 ? 1 : (gl == 3 ? -1 : 0);
-            const int ey = gl == 2 ? 1 : (gl == 4 ? -1 : 0);
-            const int dcx = (cx + ex + R.ncx) % R.ncx, dcy = (cy + ey + R.ncy) % R.ncy;
-            const int target = (gl == 0 ? pv.x : pv.y) + 1;
-            const bool dep = valid && gl < 5 && target > 0 && !(ey != 0 && R.ncy == 1);
-            if (!wait_epochs(P.epoch + R.cell_off, dcy * R.ncx + dcx, dep, target, P, lane)) break;
+            bool ok = true;
+#pragma unroll
+            for (int d0 = 0; d0 < 5; d0 += W) {
+                const int d = d0 + gl;
+                const int ex = d == 1 ? 1 : (d == 3 ? -1 : 0);
+                const int ey = d == 2 ? 1 : (d == 4 ? -1 : 0);
+                const int dcx = (cx + ex + R.ncx) % R.ncx, dcy = (cy + ey + R.ncy) % R.ncy;
+                const int target = (d == 0 ? pv.x : pv.y) + 1;
+                const bool dep = valid && d < 5 && target > 0 && !(ey != 0 && R.ncy == 1);
+                if (ok) ok = wait_epochs(P.epoch + R.cell_off, dcy * R.ncx + dcx, dep, target, P, lane);
+            }
+            if (!ok) break;
         }
         bool bad = false;
-        const uint32_t e = zgb32x4_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), valid, ccol,
-                                                P.w0 + (uint32_t)i, P.h[i], P.seed, P.lat + R.lat_off,
-                                                P.lat + R.lat_off, lane, &bad);
+        const uint32_t e = zgbm_window<RL, true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), valid, ccol,
+                                                 P.w0 + (uint32_t)i, P.h[i], P.seed, P.lat + R.lat_off,
+                                                 P.lat + R.lat_off, lane, &bad);
         if (gl == 0 && valid) P.workload[slot] = (int32_t)e;
-        zgbq_count(P.counters, lane, valid, e, bad);
+        zgbq_count<W>(P.counters, lane, valid, e, bad);
         // the warp barrier orders every lane's writes before the release
         // stores of the groups' lane 0 (release is cumulative), which
         // publish them
@@ -143,32 +157,32 @@ __global__ void __launch_bounds__(256, 4) fs_zgbq_persistent_kernel(const __grid
 
 }  // namespace
 
-size_t zgb_quad_smem_per_warp()
+size_t zgb_multi_smem_per_warp(int rl)
 {
-    return (size_t)zgbq_warp_smem();
+    return (size_t)zgbm_warp_smem(rl);
 }
 
-bool zgb_quad_shape(int qx, int qy)
+bool zgb_multi_shape(int rl, int qx, int qy)
 {
-    return zgbq_shape_ok(qx, qy);
+    return (rl == 4 || rl == 8) && zgbm_shape_ok(rl, qx, qy);
 }
 
-cudaError_t launch_zgb_quad_window(const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
+cudaError_t launch_zgb_multi_window(int rl, const WindowArgs &a, int nactive, int wpb, cudaStream_t st)
 {
-    const int quads = (nactive + 3) / 4;
-    const int blocks = (quads + wpb - 1) / wpb;
+    const int groups = (nactive + rl - 1) / rl;
+    const int blocks = (groups + wpb - 1) / wpb;
     if (blocks == 0) return cudaSuccess;
-    const int spw = (int)zgb_quad_smem_per_warp();
+    const int spw = (int)zgb_multi_smem_per_warp(rl);
     const size_t smem = (size_t)spw * wpb;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(fs_zgbq_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fs_zgbq_window_kernel<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
+    void (*kern)(WindowArgs, int, int) = rl == 8 ? fs_zgbq_window_kernel<8> : fs_zgbq_window_kernel<4>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<blocks, 32 * wpb, smem, st>>>(a, nactive, spw);
     return cudaGetLastError();
 }
 
-void *zgb_quad_persistent_kernel()
+void *zgb_multi_persistent_kernel(int rl)
 {
-    return (void *)fs_zgbq_persistent_kernel;
+    return rl == 8 ? (void *)fs_zgbq_persistent_kernel<8> : (void *)fs_zgbq_persistent_kernel<4>;
 }
 
 }  // namespace fskmc

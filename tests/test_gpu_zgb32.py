@@ -1,7 +1,7 @@
 """The register-resident binary32 windows of 32-wide ZGB cells (the batched
 form of the 16384^2 benchmark) -- one cell per warp, two cells per warp at
-two rows per lane, or four at four rows per lane -- against the binary64
-form, which is the oracle's
+two rows per lane, four at four rows per lane or eight at eight -- against
+the binary64 form, which is the oracle's
 arithmetic bit for bit: pair events on undirected bonds at twice the
 directed rate are the same process, so over many replicas from the same
 snapshot the event counts and every observable agree within 4 standard
@@ -67,9 +67,10 @@ def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T
     (64, 64, 2, "LIE"), (192, 64, 8, "STRANG"), (128, 96, 12, "RANDOM"),
 ])
 def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
-    """Plain and persistent engines, one cell per warp and several (four for
-    rows a multiple of 4 from 8, else two for an even number of rows): the
-    same lattice, event count and per-cell workloads in all four."""
+    """Plain and persistent engines, one cell per warp and several (eight in
+    the persistent engine for rows a multiple of 8 from 16, four for a
+    multiple of 4 from 8, else two for an even number of rows): the same
+    lattice, event count and per-cell workloads in all four."""
     snap = random_lattice(lx, ly, 3, 7 + qy, p=[0.6, 0.2, 0.2])
     out = []
     for engine in ("PLAIN", "PERSISTENT"):
@@ -78,9 +79,11 @@ def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
                 c.set_clock("FP32")
                 c.set_engine(engine)
                 c.set_cell_grouping(grouped)
+                oct8 = grouped and engine == "PERSISTENT" and qy % 8 == 0 and qy >= 16
                 quad = grouped and qy % 4 == 0 and qy >= 8
-                pair = grouped and not quad and qy % 2 == 0 and qy >= 4
-                assert c.info()["lanes_per_cell"] == (8 if quad else (16 if pair else 32))
+                pair = grouped and qy % 2 == 0 and qy >= 4
+                want = 4 if oct8 else (8 if quad else (16 if pair else 32))
+                assert c.info()["lanes_per_cell"] == want
                 c.set_state(snap)
                 c.run(scheme, 0.02, 0.4, 5)
                 st = c.stats()
@@ -90,7 +93,7 @@ def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
         assert np.array_equal(g, out[0][0]) and ev == out[0][1] > 0 and np.array_equal(wl, out[0][2])
 
 
-@pytest.mark.parametrize("qy", [16, 8])  # four cells per warp; 64-row replicas hold (32, 8) cells too
+@pytest.mark.parametrize("qy", [16, 8])  # eight and four cells per warp (persistent engine)
 def test_zgb32_several_cells_per_warp_batch_equals_one_cell(qy):
     """A batch of replicas of different sizes and rates in the persistent
     engine: several cells per warp equal one cell per warp, replica by
