@@ -187,11 +187,11 @@ def algo_lane_ops_per_event(model, q, fp64):
 # source they were taken on: DRAM bytes per fractional window of the
 # workload and the issue-slot utilisation.
 PROFILED = {
-    ("fs_zgbp_persistent_kernel", "zgb16384"): {
-        "src": ["fskmc_zgbpair.cu", "fskmc_zgb32x2.cuh", "fskmc_zgb32.cuh", "fskmc_device.cuh", "fskmc_internal.h",
-                "philox.cuh"],
-        "dram_bytes_per_window": 498167526, "issue_active": 0.767,
-        "src_sha256": "af5a7c38ea3ba1bee271006506458729f47ae0eb8227d82abecfd391ed845805"},
+    ("fs_zgbq_persistent_kernel<8>", "zgb16384"): {
+        "src": ["fskmc_zgbquad.cu", "fskmc_zgb32x4.cuh", "fskmc_zgb32x2.cuh", "fskmc_zgb32.cuh", "fskmc_device.cuh",
+                "fskmc_internal.h", "fskmc_logtab.h", "philox.cuh"],
+        "dram_bytes_per_window": 555474492, "issue_active": 0.647,
+        "src_sha256": "b224e5edd661df80ffecdebb01ebc9ba5791c3486029352369ec25000a3d4ff0"},
 }
 
 
