@@ -149,12 +149,20 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
         // through zgbp_bonds), the totals and the fixed-point rate sums
         uint32_t eB = __shfl_down_sync(FULLW, e[0], 1, W), aB = __shfl_down_sync(FULLW, a[0], 1, W);
         if (last) { eB = eH; aB = aH; }
+        // cl: the lane's member count of each class; pc: its count of class
+        // k in row pair p (each below 256) at bit 8 (NP k + p) of the NP words
         int cl[4] = {0, 0, 0, 0};
+        uint32_t pc[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) pc[i] = 0u;
         uint32_t lbits1 = 0u, lbits2 = 0u, n1 = 0u, n2 = 0u;
 #pragma unroll
-        for (int r = 0; r < RL; ++r) {
-            cl[0] += __popc(e[r]);
-            cl[3] += __popc(a[r]);
+        for (int p = 0; p < NP; ++p) {
+            const int s0 = __popc(e[2 * p]) + __popc(e[2 * p + 1]), s3 = __popc(a[2 * p]) + __popc(a[2 * p + 1]);
+            cl[0] += s0;
+            cl[3] += s3;
+            pc[0] += (uint32_t)s0 << (8 * p);
+            pc[3 * NP / 4] += (uint32_t)s3 << (8 * (3 * NP + p) % 32);
         }
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
@@ -166,8 +174,11 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
                                                eH, aH, hl >> (4 * p), hr >> (4 * p));
             const ZgbPairBonds B2 = zgbp_bonds(2, pl, pf, ew, e[2 * p], a[2 * p], e[2 * p + 1], a[2 * p + 1], be, ba,
                                                eH, aH, hl >> (4 * p), hr >> (4 * p));
-            cl[1] += zgbp_bond_count(B1);
-            cl[2] += zgbp_bond_count(B2);
+            const int c1 = zgbp_bond_count(B1), c2 = zgbp_bond_count(B2);
+            cl[1] += c1;
+            cl[2] += c2;
+            pc[NP / 4] += (uint32_t)c1 << (8 * (NP + p) % 32);
+            pc[2 * NP / 4] += (uint32_t)c2 << (8 * (2 * NP + p) % 32);
             bq[32 * p + lane] = make_uint4(B1.H0, B1.H1, B1.V0, B1.V1);  // lane-contiguous: no bank conflicts
             bq[32 * NP + 32 * p + lane] = make_uint4(B2.H0, B2.H1, B2.V0, B2.V1);
             lbits1 |= B1.L << (2 * p);
@@ -233,40 +244,55 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
         int code = 0;
         if (live && l == owner) {
             int r = (int)j - (incl - c);
-            uint32_t msk = 0u;
-            int kind = 0, rr = 0;
-            bool found = false;
-            if (k == 0 || k == 3) {
+            // the row pair that holds the lane's member r, from the pair
+            // counts, then the member among the pair's entries
+            uint32_t pk = 0u;
 #pragma unroll
-                for (int q = 0; q < RL; ++q) {
-                    const uint32_t m = k == 0 ? e[q] : a[q];
-                    const int cq = __popc(m);
-                    if (!found) {
-                        if (r < cq) { msk = m; rr = q; found = true; }
-                        else r -= cq;
-                    }
-                }
-            } else {
-                // the lane's members of class k as counted above, row by row:
-                // each row's horizontal bonds, the vertical bonds below it, its
-                // left cross bond, and for row 0 the top-halo bonds
-                const uint2 ln = bln[(k - 1) * 32 + lane];
+            for (int i = 0; i < NP; ++i)
+                if (k * NP / 4 == i) pk = pc[i];
+            pk >>= 8 * (k * NP) % 32;
+            int p = 0;
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const uint4 q = bq[(k - 1) * 32 * NP + 32 * p + lane];
-                    const uint32_t ms[7] = {q.x, q.z, (ln.x >> (2 * p)) & 1u, p == 0 ? ln.y : 0u,
-                                            q.y, q.w, (ln.x >> (2 * p + 1)) & 1u};
-                    const int kd[7] = {1, 2, 4, 5, 1, p < NP - 1 ? 2 : 3, 4};
-#pragma unroll
-                    for (int u = 0; u < 7; ++u) {
-                        const int cq = __popc(ms[u]);
-                        if (!found) {
-                            if (r < cq) { msk = ms[u]; kind = kd[u]; rr = 2 * p + (u < 4 ? 0 : 1); found = true; }
-                            else r -= cq;
-                        }
-                    }
+            for (int q = 0; q < NP - 1; ++q) {
+                const int cq = (int)((pk >> (8 * q)) & 0xFFu);
+                if (p == q && r >= cq) {
+                    r -= cq;
+                    p = q + 1;
                 }
             }
+            // a site class's entries: the pair's two rows; a pair class's: row
+            // 2p's horizontal bonds, the vertical bonds below it, its left
+            // cross bond, for p = 0 the top-halo bonds, then row 2p + 1's
+            // horizontal, vertical and left cross bonds
+            const bool site = k == 0 || k == 3;
+            uint32_t s0 = 0u, s1 = 0u;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (p == q) {
+                    s0 = k == 0 ? e[2 * q] : a[2 * q];
+                    s1 = k == 0 ? e[2 * q + 1] : a[2 * q + 1];
+                }
+            }
+            const int kb = site ? 0 : k - 1;
+            const uint4 qv = bq[kb * 32 * NP + 32 * p + lane];
+            const uint2 ln = bln[kb * 32 + lane];
+            const uint32_t ms[7] = {site ? s0 : qv.x, site ? 0u : qv.z, site ? 0u : (ln.x >> (2 * p)) & 1u,
+                                    (site || p != 0) ? 0u : ln.y, site ? s1 : qv.y, site ? 0u : qv.w,
+                                    site ? 0u : (ln.x >> (2 * p + 1)) & 1u};
+            uint32_t msk = 0u;
+            int u0 = 0;
+            bool found = false;
+#pragma unroll
+            for (int u = 0; u < 7; ++u) {
+                const int cq = __popc(ms[u]);
+                if (!found) {
+                    if (r < cq) { msk = ms[u]; u0 = u; found = true; }
+                    else r -= cq;
+                }
+            }
+            const int rr = 2 * p + (u0 >= 4 ? 1 : 0);
+            const int kind = site ? 0 : (u0 == 1 || u0 == 5 ? ((u0 == 5 && p == NP - 1) ? 3 : 2)
+                                                           : (u0 == 2 || u0 == 6 ? 4 : (u0 == 3 ? 5 : 1)));
             code = (kind << 8) | (rr << 5) | select_bit(msk, r);
         }
         code = __shfl_sync(FULLW, code, owner, W);
