@@ -299,48 +299,42 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
         if (live) {
             const int kind = code >> 8, rr = (code >> 5) & 7, x = code & 31;
             const uint32_t bit = 1u << x;
-            if (kind == 0) {
-                if (l == owner) {
-                    // A adsorbs on an empty site (class 0) or desorbs (class 3)
-                    const bool toA = k == 0;
-#pragma unroll
-                    for (int q = 0; q < RL; ++q) {
-                        const uint32_t m = rr == q ? bit : 0u;
-                        e[q] = toA ? (e[q] & ~m) : (e[q] | m);
-                        a[q] = toA ? (a[q] | m) : (a[q] & ~m);
-                    }
-                }
-            } else {
-                // B2 adsorption makes both ends B, the reaction both ends empty
-                const bool toB = k == 1;
+            // the changed sites' new state: A (class 0, adsorption), empty
+            // (class 3, desorption; class 2, the reaction) or B (class 1, B2
+            // adsorption: neither mask)
+            const uint32_t setE = k >= 2 ? ~0u : 0u, setA = k == 0 ? ~0u : 0u;
+            // this lane's changed sites: mA in its row r1, mB in row r1 + 1
+            int r1 = -2;
+            uint32_t mA = 0u, mB = 0u;
+            if (l == owner) {
+                // the sites of the member's row rr (a site; both ends of a
+                // horizontal bond; the site of a cross or top-halo bond; the
+                // upper end of a vertical one) and, for a vertical bond within
+                // the lane, of row rr + 1; and the halo sites the bond changes
+                r1 = rr;
+                mA = kind == 1 ? (bit | (x < 31 ? bit << 1 : 0u)) : (kind == 4 ? 1u : bit);
+                mB = kind == 2 ? bit : 0u;
                 const uint32_t hrc = (kind == 1 && x == 31) ? 3u << (2 * rr) : 0u;
                 const uint32_t hlc = kind == 4 ? 3u << (2 * rr) : 0u;
-                const bool hrow = kind == 5 || (kind == 3 && last);
-                const uint32_t hval = toB ? 0u : 0x5555u;  // empty: bit 2r of a pair; B: neither
-                if (l == owner) {
-                    // the sites of the member's row rr (both ends of a horizontal
-                    // bond, the site of a cross or top-halo bond, the upper end
-                    // of a vertical one) and, for a vertical bond within the
-                    // lane, of row rr + 1
-                    const uint32_t mA = kind == 1 ? (bit | (x < 31 ? bit << 1 : 0u)) : (kind == 4 ? 1u : bit);
-                    const uint32_t mB = kind == 2 ? bit : 0u;
-#pragma unroll
-                    for (int q = 0; q < RL; ++q) {
-                        const uint32_t m = (rr == q ? mA : 0u) | (rr + 1 == q ? mB : 0u);
-                        e[q] = toB ? (e[q] & ~m) : (e[q] | m);
-                        a[q] &= ~m;
-                    }
-                    hr = (hr & ~hrc) | (hval & hrc);
-                    hl = (hl & ~hlc) | (hval & hlc);
-                    if (hrow) { eH = toB ? (eH & ~bit) : (eH | bit); aH &= ~bit; }
+                const uint32_t hval = k == 1 ? 0u : 0x5555u;  // empty: bit 2r of a pair; B: neither
+                hr = (hr & ~hrc) | (hval & hrc);
+                hl = (hl & ~hlc) | (hval & hlc);
+                if (kind == 5 || (kind == 3 && last)) {
+                    eH = (eH & ~bit) | (bit & setE);
+                    aH &= ~bit;
                 }
-                // the lower end of a vertical bond below the owner's last row,
-                // unless the owner holds the cell's last row (the bottom halo
+            } else if (kind == 3 && owner != nrl - 1 && l == owner + 1) {
+                // the lower end of a vertical bond below the owner's last row
+                // (unless the owner holds the cell's last row: the bottom halo
                 // row, changed above)
-                if (kind == 3 && owner != nrl - 1 && l == owner + 1) {
-                    e[0] = toB ? (e[0] & ~bit) : (e[0] | bit);
-                    a[0] &= ~bit;
-                }
+                r1 = -1;
+                mB = bit;
+            }
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const uint32_t m = (r1 == q ? mA : 0u) | (r1 + 1 == q ? mB : 0u);
+                e[q] = (e[q] & ~m) | (m & setE);
+                a[q] = (a[q] & ~m) | (m & setA);
             }
             ++ev;
         }
