@@ -5,7 +5,7 @@
 //
 // This is zgb32x2_window (fskmc_zgb32x2.cuh) with RL rows per lane and RL
 // cells per warp: the same classes from bit masks (each pair of rows through
-// zgbp_bonds), the same undirected bonds at twice the directed rate, the
+// zgbm_pair_bonds), the same undirected bonds at twice the directed rate, the
 // same draws (event e of a cell draws Philox counter e), the same fixed-point
 // class sums, binary32 clock and member numbering (row by row), so it gives
 // the lattices of the one- and two-cell kernels. The cells step in lockstep,
@@ -66,10 +66,40 @@ __device__ __forceinline__ uint4 zgbq_ld16(const uint8_t *p)
     return *q;
 }
 
-// A site's halo code: bit 0 empty, bit 1 A (B neither).
-__device__ __forceinline__ uint32_t zgbq_hcode(uint8_t s)
+// A lane's members of the two pair classes in its rows r, r + 1 (empty
+// masks e0, e1, A masks a0, a1), except the left cross bonds: the
+// horizontal bonds of each row (bond 31 to the right halo site, owned in E
+// windows), the vertical bonds between the two rows and below row r + 1
+// (eB, aB: the row below; crossing to the bottom halo in the cell's last
+// row, owned in O windows), and for the cell's row 0 the vertical bonds to
+// the top halo row eN, aN (O windows). hre, hra: bit 0 (1) set if the right
+// halo site of row r (r + 1) is empty / holds A. B2 adsorption takes an
+// empty-empty bond; the reaction an A-B bond, i.e. one end A and neither
+// end empty.
+struct ZgbmPair {
+    uint32_t H0, H1, V0, V1, N;
+};
+
+__device__ __forceinline__ void zgbm_pair_bonds(bool last, bool first, bool ew, uint32_t e0, uint32_t a0, uint32_t e1,
+                                                uint32_t a1, uint32_t eB, uint32_t aB, uint32_t eN, uint32_t aN,
+                                                uint32_t hre, uint32_t hra, ZgbmPair &B1, ZgbmPair &B2)
 {
-    return (uint32_t)(s == 0) | ((uint32_t)(s == 1) << 1);
+    // right neighbours of every site of a row: site 31's is the right halo site
+    const uint32_t eR0 = __funnelshift_r(e0, hre, 1), aR0 = __funnelshift_r(a0, hra, 1);
+    const uint32_t eR1 = __funnelshift_r(e1, hre >> 1, 1), aR1 = __funnelshift_r(a1, hra >> 1, 1);
+    const uint32_t ownH = ew ? ~0u : 0x7FFFFFFFu;
+    const uint32_t ownV1 = (!last || !ew) ? ~0u : 0u;
+    const uint32_t ownN = (first && !ew) ? ~0u : 0u;
+    B1.H0 = e0 & eR0 & ownH;
+    B1.H1 = e1 & eR1 & ownH;
+    B1.V0 = e0 & e1;
+    B1.V1 = e1 & eB & ownV1;
+    B1.N = eN & e0 & ownN;
+    B2.H0 = (a0 ^ aR0) & ~(e0 | eR0) & ownH;
+    B2.H1 = (a1 ^ aR1) & ~(e1 | eR1) & ownH;
+    B2.V0 = (a0 ^ a1) & ~(e0 | e1);
+    B2.V1 = (a1 ^ aB) & ~(e1 | eB) & ownV1;
+    B2.N = (aN ^ a0) & ~(eN | e0) & ownN;
 }
 
 
@@ -98,9 +128,9 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
 
     // The lane's rows and their halo sites, loaded from global memory into
     // registers; local lane 0 also the halo row above the cell, the last row
-    // lane the one below. hl, hr: row r's left / right halo site at bits 2r
-    // (empty), 2r + 1 (A).
-    uint32_t e[RL], a[RL], eH = 0u, aH = 0u, hl = 0u, hr = 0u;
+    // lane the one below. hx: bit r (8 + r) set if row r's left halo site is
+    // empty (holds A), bit 16 + r (24 + r) if its right halo site is.
+    uint32_t e[RL], a[RL], eH = 0u, aH = 0u, hx = 0u;
 #pragma unroll
     for (int r = 0; r < RL; ++r) { e[r] = 0u; a[r] = 0u; }
     if (row) {
@@ -112,8 +142,8 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
             const uint4 u0 = zgbq_ld16<PERSIST>(p + X0), u1 = zgbq_ld16<PERSIST>(p + X0 + 16);
             const uint8_t sl = ld_site<PERSIST>(p + gxl), sr = ld_site<PERSIST>(p + gxr);
             zgbq_masks(u0, u1, e[r], a[r]);
-            hl |= zgbq_hcode(sl) << (2 * r);
-            hr |= zgbq_hcode(sr) << (2 * r);
+            hx |= ((uint32_t)(sl == 0) | ((uint32_t)(sl == 1) << 8) | ((uint32_t)(sr == 0) << 16) |
+                   ((uint32_t)(sr == 1) << 24)) << r;
         }
         if (first || last) {
             const int hy = first ? (Y0 > 0 ? Y0 - 1 : ly - 1) : (Y0 + qy < ly ? Y0 + qy : 0);
@@ -146,16 +176,29 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
     bool live = valid, bad = false;
     while (__any_sync(FULLW, live)) {
         // this cell's classes: each lane's member counts (its row pairs
-        // through zgbp_bonds), the totals and the fixed-point rate sums
+        // through zgbm_pair_bonds, its rows' left cross bonds), the totals and
+        // the fixed-point rate sums
         uint32_t eB = __shfl_down_sync(FULLW, e[0], 1, W), aB = __shfl_down_sync(FULLW, a[0], 1, W);
         if (last) { eB = eH; aB = aH; }
+        // the left cross bonds of the lane's rows (owned in E windows), bit r
+        // for row r: its site 0 (gathered into ce, ca) and left halo site
+        uint32_t ce = 0u, ca = 0u;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            ce = __funnelshift_r(ce, e[r], 1);
+            ca = __funnelshift_r(ca, a[r], 1);
+        }
+        ce >>= 32 - RL;
+        ca >>= 32 - RL;
+        const uint32_t ownL = ew ? 0xFFu : 0u, hle = hx & 0xFFu, hla = (hx >> 8) & 0xFFu;
+        const uint32_t lbits1 = hle & ce & ownL, lbits2 = (hla ^ ca) & ~(hle | ce) & ownL;
         // cl: the lane's member count of each class; pc: its count of class
         // k in row pair p (each below 256) at bit 8 (NP k + p) of the NP words
         int cl[4] = {0, 0, 0, 0};
         uint32_t pc[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) pc[i] = 0u;
-        uint32_t lbits1 = 0u, lbits2 = 0u, n1 = 0u, n2 = 0u;
+        uint32_t n1 = 0u, n2 = 0u;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
             const int s0 = __popc(e[2 * p]) + __popc(e[2 * p + 1]), s3 = __popc(a[2 * p]) + __popc(a[2 * p + 1]);
@@ -169,21 +212,23 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
             // rows 2p, 2p + 1; the row below is the lane's row 2p + 2, or the
             // next lane's row 0 (the bottom halo row in the last row lane)
             const uint32_t be = p < NP - 1 ? e[2 * p + 2] : eB, ba = p < NP - 1 ? a[2 * p + 2] : aB;
-            const bool pf = p == 0 && first, pl = p == NP - 1 && last;
-            const ZgbPairBonds B1 = zgbp_bonds(1, pl, pf, ew, e[2 * p], a[2 * p], e[2 * p + 1], a[2 * p + 1], be, ba,
-                                               eH, aH, hl >> (4 * p), hr >> (4 * p));
-            const ZgbPairBonds B2 = zgbp_bonds(2, pl, pf, ew, e[2 * p], a[2 * p], e[2 * p + 1], a[2 * p + 1], be, ba,
-                                               eH, aH, hl >> (4 * p), hr >> (4 * p));
-            const int c1 = zgbp_bond_count(B1), c2 = zgbp_bond_count(B2);
+            ZgbmPair B1, B2;
+            zgbm_pair_bonds(p == NP - 1 && last, p == 0 && first, ew, e[2 * p], a[2 * p], e[2 * p + 1], a[2 * p + 1],
+                            be, ba, eH, aH, hx >> (16 + 2 * p), hx >> (24 + 2 * p), B1, B2);
+            int c1 = __popc(B1.H0) + __popc(B1.H1) + __popc(B1.V0) + __popc(B1.V1) + __popc((lbits1 >> (2 * p)) & 3u);
+            int c2 = __popc(B2.H0) + __popc(B2.H1) + __popc(B2.V0) + __popc(B2.V1) + __popc((lbits2 >> (2 * p)) & 3u);
+            if (p == 0) {
+                n1 = B1.N;
+                n2 = B2.N;
+                c1 += __popc(n1);
+                c2 += __popc(n2);
+            }
             cl[1] += c1;
             cl[2] += c2;
             pc[NP / 4] += (uint32_t)c1 << (8 * (NP + p) % 32);
             pc[2 * NP / 4] += (uint32_t)c2 << (8 * (2 * NP + p) % 32);
             bq[32 * p + lane] = make_uint4(B1.H0, B1.H1, B1.V0, B1.V1);  // lane-contiguous: no bank conflicts
             bq[32 * NP + 32 * p + lane] = make_uint4(B2.H0, B2.H1, B2.V0, B2.V1);
-            lbits1 |= B1.L << (2 * p);
-            lbits2 |= B2.L << (2 * p);
-            if (p == 0) { n1 = B1.N; n2 = B2.N; }
         }
         bln[lane] = make_uint2(lbits1, n1);
         bln[32 + lane] = make_uint2(lbits2, n2);
@@ -314,11 +359,9 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
                 r1 = rr;
                 mA = kind == 1 ? (bit | (x < 31 ? bit << 1 : 0u)) : (kind == 4 ? 1u : bit);
                 mB = kind == 2 ? bit : 0u;
-                const uint32_t hrc = (kind == 1 && x == 31) ? 3u << (2 * rr) : 0u;
-                const uint32_t hlc = kind == 4 ? 3u << (2 * rr) : 0u;
-                const uint32_t hval = k == 1 ? 0u : 0x5555u;  // empty: bit 2r of a pair; B: neither
-                hr = (hr & ~hrc) | (hval & hrc);
-                hl = (hl & ~hlc) | (hval & hlc);
+                // a bond's ends become empty or B
+                const uint32_t hm = (kind == 1 && x == 31) ? 1u << (16 + rr) : (kind == 4 ? 1u << rr : 0u);
+                hx = (hx & ~(hm * 0x101u)) | (hm & setE);
                 if (kind == 5 || (kind == 3 && last)) {
                     eH = (eH & ~bit) | (bit & setE);
                     aH &= ~bit;
@@ -352,9 +395,9 @@ __device__ uint32_t zgbm_window(uint8_t *wsm, const Replica &R, const CellGeom &
             const int gxl = X0 > 0 ? X0 - 1 : lx - 1, gxr = X0 + 32 < lx ? X0 + 32 : 0;
 #pragma unroll
             for (int r = 0; r < RL; ++r) {
-                const uint32_t cl2 = hl >> (2 * r), cr2 = hr >> (2 * r);
-                out[(int64_t)(y0 + r) * lx + gxl] = (uint8_t)((cl2 & 1u) ? 0 : ((cl2 & 2u) ? 1 : 2));
-                out[(int64_t)(y0 + r) * lx + gxr] = (uint8_t)((cr2 & 1u) ? 0 : ((cr2 & 2u) ? 1 : 2));
+                const uint32_t h = hx >> r;
+                out[(int64_t)(y0 + r) * lx + gxl] = (uint8_t)((h & 1u) ? 0 : ((h & 0x100u) ? 1 : 2));
+                out[(int64_t)(y0 + r) * lx + gxr] = (uint8_t)((h & 0x10000u) ? 0 : ((h & 0x1000000u) ? 1 : 2));
             }
         } else {
             if (first) zgb_store_row(out + (int64_t)(Y0 > 0 ? Y0 - 1 : ly - 1) * lx + X0, eH, aH);
