@@ -168,8 +168,10 @@ fskmc_status fskmc_set_warps_per_block(fskmc_ctx *ctx, int32_t warps);
    rounded up to a power of two; at least 8 in 2D, 4 on a ring) and a warp
    runs 32/W cells of the same window in lockstep, so each instruction of
    the event loop (Eqs. totalrate and skeleton per cell) serves 32/W cells.
-   ZGB with the binary32 clock and 32-wide cells of an even number of rows
-   (4 to 32), mode = 1: two cells per warp, 16 lanes each holding two rows.
+   ZGB with the binary32 clock and 32-wide cells, mode = 1: eight cells per
+   warp (4 lanes each holding eight rows) for rows a multiple of 8 from 16,
+   else four (8 lanes, four rows each) for a multiple of 4 from 8, else two
+   (16 lanes, two rows each) for an even number from 4 to 32.
    mode = 0: one cell per warp. mode = 2 (default, auto): the same as 1
    (faster in every engine and clock measured). Diffusion, ZGB otherwise,
    and larger cells always take a whole warp. Results (lattices, event

@@ -417,9 +417,9 @@ int lanes_per_cell(const fskmc_ctx *c)
     // an even number of rows; fskmc_zgbpair.cu)
     if (c->model == FSKMC_ZGB) {
         if (c->clock != FSKMC_CLOCK_FP32) return 32;
-        // the persistent engine: eight cells per warp, 4 lanes each (1-2%
-        // faster there than four); the plain engine: four, 8 lanes each
-        if (c->engine == FSKMC_ENGINE_PERSISTENT && fskmc::zgb_multi_shape(8, c->qx, c->qy)) return 4;
+        // eight cells per warp, 4 lanes each (rows a multiple of 8 from 16),
+        // else four, 8 lanes each (a multiple of 4 from 8), else two
+        if (fskmc::zgb_multi_shape(8, c->qx, c->qy)) return 4;
         if (fskmc::zgb_multi_shape(4, c->qx, c->qy)) return 8;
         return fskmc::zgb_pair_shape(c->qx, c->qy) ? 16 : 32;
     }

@@ -36,9 +36,10 @@ __device__ __forceinline__ void zgbq_count(unsigned long long *counters, int lan
     }
 }
 
-// Held to 64 registers (as the other one-window kernels).
+// Held to 64 registers (as the other one-window kernels) with four cells
+// per warp, to 80 with eight, where 64 would spill.
 template <int RL>
-__global__ void __launch_bounds__(512, 2) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
+__global__ void __launch_bounds__(RL == 8 ? 256 : 512, RL == 8 ? 3 : 2) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
     constexpr int W = 32 / RL;
     extern __shared__ __align__(16) uint8_t smem[];

@@ -178,7 +178,7 @@ def test_grouping_switch_rejects_bad_values():
     with F.Context(64, 64, "ZGB", dict(yA=0.5, kr=1.0, kd=0.0), (32, 32)) as c:
         assert c.info()["lanes_per_cell"] == 32  # binary64 clock: one cell per warp
         c.set_clock("FP32")
-        assert c.info()["lanes_per_cell"] == 8  # four 32-wide cells per warp
+        assert c.info()["lanes_per_cell"] == 4  # eight 32-wide cells per warp
         c.set_cell_grouping(False)
         assert c.info()["lanes_per_cell"] == 32
 

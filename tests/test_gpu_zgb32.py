@@ -67,10 +67,10 @@ def test_zgb32_binary32_matches_binary64_statistically(lx, ly, qy, scheme, dt, T
     (64, 64, 2, "LIE"), (192, 64, 8, "STRANG"), (128, 96, 12, "RANDOM"),
 ])
 def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
-    """Plain and persistent engines, one cell per warp and several (eight in
-    the persistent engine for rows a multiple of 8 from 16, four for a
-    multiple of 4 from 8, else two for an even number of rows): the same
-    lattice, event count and per-cell workloads in all four."""
+    """Plain and persistent engines, one cell per warp and several (eight for
+    rows a multiple of 8 from 16, four for a multiple of 4 from 8, else two
+    for an even number of rows): the same lattice, event count and per-cell
+    workloads in all four."""
     snap = random_lattice(lx, ly, 3, 7 + qy, p=[0.6, 0.2, 0.2])
     out = []
     for engine in ("PLAIN", "PERSISTENT"):
@@ -79,7 +79,7 @@ def test_zgb32_engines_and_windows_agree_bitwise(lx, ly, qy, scheme):
                 c.set_clock("FP32")
                 c.set_engine(engine)
                 c.set_cell_grouping(grouped)
-                oct8 = grouped and engine == "PERSISTENT" and qy % 8 == 0 and qy >= 16
+                oct8 = grouped and qy % 8 == 0 and qy >= 16
                 quad = grouped and qy % 4 == 0 and qy >= 8
                 pair = grouped and qy % 2 == 0 and qy >= 4
                 want = 4 if oct8 else (8 if quad else (16 if pair else 32))
