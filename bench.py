@@ -185,13 +185,13 @@ def algo_lane_ops_per_event(model, q, fp64):
 
 # ncu figures of the bench's kernels (profiles/), valid only for the kernel
 # source they were taken on: DRAM bytes per fractional window of the
-# workload and the issue-slot utilisation.
+# workload, the issue-slot utilisation and the ALU pipe's utilisation.
 PROFILED = {
     ("fs_zgbq_persistent_kernel<8>", "zgb16384"): {
         "src": ["fskmc_zgbquad.cu", "fskmc_zgb32x4.cuh", "fskmc_zgb32x2.cuh", "fskmc_zgb32.cuh", "fskmc_device.cuh",
                 "fskmc_internal.h", "fskmc_logtab.h", "philox.cuh"],
-        "dram_bytes_per_window": 555474492, "issue_active": 0.647,
-        "src_sha256": "b224e5edd661df80ffecdebb01ebc9ba5791c3486029352369ec25000a3d4ff0"},
+        "dram_bytes_per_window": 560612736, "issue_active": 0.659, "alu_pipe": 0.769,
+        "src_sha256": "1ad761db265fe052d528224d70b5f7b9b627cf03b403a5b2d739a6058cbcbeb6"},
 }
 
 
@@ -521,11 +521,12 @@ def run_workload(args, rank, world, local):
     ops = algo_lane_ops_per_event(w["model"], w["q"], fp64)
     achieved = ev_launch * ops / launch_s / 1e9
     prof = PROFILED.get((kname, args.workload))
-    traffic = issue = None
+    traffic = issue = alu = None
     if prof and prof["src_sha256"] and prof["src_sha256"] == src_sha(prof["src"]):
         if prof["dram_bytes_per_window"]:
             traffic = prof["dram_bytes_per_window"] * nwin_step / launches_per_step
         issue = prof["issue_active"]
+        alu = prof.get("alu_pipe")
     active_cells = info["cells"] // 2
     comparisons = {}
     for f, r in res.items():
@@ -569,7 +570,7 @@ def run_workload(args, rank, world, local):
                      "kernel": kname, "kernel_ms_avg": launch_s * 1000,
                      "launches_per_step": launches_per_step, "events_per_launch": ev_launch,
                      "algorithmic_lane_ops_per_event": ops,
-                     "issue_active_ncu": issue,
+                     "issue_active_ncu": issue, "alu_pipe_ncu": alu,
                      "peak_note": "derived: 152 SMs x 128 lanes x 2.07 GHz (plain ALU lanes; the "
                                   "path has no dense contraction)",
                      "hbm_note": f"{sb:.2f} algorithmic bytes per active site per window; "
