@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
             ok = wait_epochs(ep, dcy * R.ncx + dcx, dep, target, P, lane);
         } else {
             // ping-pong: every cell has a task in every window and
-            // epoch[c] = 1 + the last window whose reads and writes of cell
-            // c's sites are complete; active cells wait on their 3x3
-            // neighbourhood
+            // epoch[c] = 1 + the last window whose task of cell c is
+            // complete (an active cell's window, an inactive cell's copy);
+            // every task waits on its 3x3 neighbourhood
             const int ddx = lane % 3 - 1, ddy = lane / 3 - 1;
             const int dcx = (cx + ddx + R.ncx) % R.ncx, dcy = (cy + ddy + R.ncy) % R.ncy;
             ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 9, i, P, lane);
@@ -227,13 +227,13 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
                 if (nexact) atomicAdd(&P.counters[4], (unsigned long long)nexact);
             }
         } else {
+            // An inactive cell publishes its window as soon as its copy is
+            // done. Whoever next reads or overwrites the sites its active
+            // edge neighbours write into it (its edge band, its corners)
+            // waits on those neighbours too: every later task waits on its
+            // whole 3x3 neighbourhood, and the cells reading this cell's
+            // corners have the writers of those corners as edge neighbours.
             copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.geom.qx, P.geom.qy, cx, cy, wcol, lane);
-            // the active edge neighbours write into this cell: wait for them
-            int ex = lane == 0 ? 1 : (lane == 1 ? -1 : 0);
-            int ey = lane == 2 ? 1 : (lane == 3 ? -1 : 0);
-            int ncx2 = (cx + ex + R.ncx) % R.ncx, ncy2 = (cy + ey + R.ncy) % R.ncy;
-            ok = wait_epochs(ep, ncy2 * R.ncx + ncx2, lane < 4, i + 1, P, lane);
-            if (!ok) break;
         }
         // the warp barrier orders every lane's writes before lane 0's release
         // store (release is cumulative), which publishes them
