@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
     uint8_t *wsm = smem + (size_t)wib * smem_per_warp;
     const bool pingpong = P.lat2 != nullptr;
     const bool inplace = P.inplace != 0;
-    const int per_window = inplace ? P.total_active : P.total_cells;
+    // One task per active cell and window; with ping-pong storage the task
+    // also copies the unwritten sites of the inactive cell to its right
+    // (each inactive cell is the right neighbour of exactly one active cell).
+    const int per_window = P.total_active;
     const unsigned long long total = (unsigned long long)P.nwin * (unsigned long long)per_window;
 
     // In-place models with the binary64 clock: the next task is dequeued
@@ -155,17 +158,14 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
         if (__shfl_sync(0xffffffffu, ab, 0)) break;
         const int i = (int)(t / (unsigned long long)per_window);
         const int u = (int)(t % (unsigned long long)per_window);
-        const bool active = u < P.total_active;
-        const int a = active ? u : u - P.total_active;
-        const int2 rk = P.cell_rk[a];
+        const int2 rk = P.cell_rk[u];
         const int r = rk.x;
         const int k = rk.y;
         const Replica &R = P.reps[r];
         const int64_t widx = P.colour_per_replica ? (int64_t)r * P.nwin + i : i;
-        const int wcol = P.colour[widx];
-        const int ccol = active ? wcol : 1 - wcol;
+        const int ccol = P.colour[widx];
         int cx, cy;
-        if (active && P.order) {
+        if (P.order) {
             const int mo = P.order[R.cell_off + ccol * ((R.ncx >> 1) * R.ncy) + k];
             cy = mo / R.ncx;
             cx = mo - cy * R.ncx;
@@ -196,44 +196,45 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
             const bool dep = lane < 5 && target > 0 && !(ey != 0 && R.ncy == 1);
             ok = wait_epochs(ep, dcy * R.ncx + dcx, dep, target, P, lane);
         } else {
-            // ping-pong: every cell has a task in every window and
-            // epoch[c] = 1 + the last window whose task of cell c is
-            // complete (an active cell's window, an inactive cell's copy);
-            // every task waits on its 3x3 neighbourhood
-            const int ddx = lane % 3 - 1, ddy = lane / 3 - 1;
+            // ping-pong: epoch[c] = 1 + the last window whose work on cell c
+            // is complete (an active cell's window, an inactive cell's
+            // copy). The active cell and the inactive cell to its right each
+            // need their 3x3 neighbourhood done with the previous window: the
+            // 4 x 3 cells from one left of this cell to two right of it.
+            const int ddx = (lane & 3) - 1, ddy = (lane >> 2) - 1;
             const int dcx = (cx + ddx + R.ncx) % R.ncx, dcy = (cy + ddy + R.ncy) % R.ncy;
-            ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 9, i, P, lane);
+            ok = wait_epochs(ep, dcy * R.ncx + dcx, lane < 12, i, P, lane);
         }
         if (!ok) break;
-        if (active) {
-            bool amb = false, bad = false;
-            uint32_t nexact = 0;
-            uint32_t e;
-            if constexpr (ROWREG && MODEL == DIFFUSION)
-                e = diff32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
-                                        P.h[i], P.seed, cur, nxt, lane, &bad);
-            else if constexpr (ROWREG)
-                e = zgb32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
-                                       P.h[i], P.seed, cur, nxt, lane, &bad);
-            else
-                e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol,
-                                                          P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
-                                                          cur, nxt, lane, &amb, &bad, &nexact);
-            if (lane == 0) {
-                P.workload[slot] = (int32_t)e;
-                atomicAdd(&P.counters[0], (unsigned long long)e);
-                if (amb) atomicAdd(&P.counters[1], 1ull);
-                if (bad) atomicAdd(&P.counters[3], 1ull);
-                if (nexact) atomicAdd(&P.counters[4], (unsigned long long)nexact);
-            }
-        } else {
-            // An inactive cell publishes its window as soon as its copy is
-            // done. Whoever next reads or overwrites the sites its active
-            // edge neighbours write into it (its edge band, its corners)
-            // waits on those neighbours too: every later task waits on its
-            // whole 3x3 neighbourhood, and the cells reading this cell's
-            // corners have the writers of those corners as edge neighbours.
-            copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.geom.qx, P.geom.qy, cx, cy, wcol, lane);
+        bool amb = false, bad = false;
+        uint32_t nexact = 0;
+        uint32_t e;
+        if constexpr (ROWREG && MODEL == DIFFUSION)
+            e = diff32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
+                                    P.h[i], P.seed, cur, nxt, lane, &bad);
+        else if constexpr (ROWREG)
+            e = zgb32_window<true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol, P.w0 + (uint32_t)i,
+                                   P.h[i], P.seed, cur, nxt, lane, &bad);
+        else
+            e = cell_window<MODEL, CLK, true, PACKED>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), ccol,
+                                                      P.w0 + (uint32_t)i, P.h[i], P.screen != 0, P.seed,
+                                                      cur, nxt, lane, &amb, &bad, &nexact);
+        if (lane == 0) {
+            P.workload[slot] = (int32_t)e;
+            atomicAdd(&P.counters[0], (unsigned long long)e);
+            if (amb) atomicAdd(&P.counters[1], 1ull);
+            if (bad) atomicAdd(&P.counters[3], 1ull);
+            if (nexact) atomicAdd(&P.counters[4], (unsigned long long)nexact);
+        }
+        if (pingpong) {
+            // the inactive cell to the right. It publishes its window as soon
+            // as its copy is done: whoever next reads or overwrites the sites
+            // its active edge neighbours write into it (its edge band, its
+            // corners) waits on those neighbours too, since every task waits
+            // on the 3x3 neighbourhood of the cells it works on and the cells
+            // reading this cell's corners have the writers of those corners
+            // as edge neighbours.
+            copy_unwritten<true>(cur, nxt, R.lx, R.ly, P.geom.qx, P.geom.qy, (cx + 1) % R.ncx, cy, ccol, lane);
         }
         // the warp barrier orders every lane's writes before lane 0's release
         // store (release is cumulative), which publishes them
@@ -241,6 +242,10 @@ __global__ void __launch_bounds__(256, 4) fs_persistent_kernel(const __grid_cons
         if (lane == 0) {
             cuda::atomic_ref<int32_t, cuda::thread_scope_device> ea(P.epoch[slot]);
             ea.store(i + 1, cuda::memory_order_release);
+        }
+        if (pingpong && lane == 1) {
+            cuda::atomic_ref<int32_t, cuda::thread_scope_device> eb(P.epoch[R.cell_off + cy * R.ncx + (cx + 1) % R.ncx]);
+            eb.store(i + 1, cuda::memory_order_release);
         }
     }
 }
