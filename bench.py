@@ -350,10 +350,12 @@ def make_ctx(F, w, form, stream, seed, args):
     return c
 
 
-def time_form(F, w, form, stream, seed, args, flush, world, clk=None):
+def time_form(F, w, form, stream, seed, args, flush, world, clk=None, snapshot=None):
     """W untimed steps, then K steps each bracketed by CUDA events on the
     context's stream (L2 flushed between steps, outside the events): one step
-    = fskmc_run over 10 dt + the observables. Returns the form's figures."""
+    = fskmc_run over 10 dt + the observables. Returns the form's figures;
+    `snapshot` (host array), if given, receives the lattice the timed steps
+    start from."""
     import torch
     ctx = make_ctx(F, w, form, stream, seed, args)
     step_t = STEP_WINDOWS_DT * w["dt"]
@@ -361,6 +363,8 @@ def time_form(F, w, form, stream, seed, args, flush, world, clk=None):
         ctx.run(w["scheme"], w["dt"], step_t, seed)
         ctx.observables(0, RMAX)
     torch.cuda.synchronize()
+    if snapshot is not None:
+        ctx.get_state(0, snapshot)
     st0 = ctx.stats()
     barrier(world)
     marks = []
@@ -389,16 +393,13 @@ def time_form(F, w, form, stream, seed, args, flush, world, clk=None):
     return out
 
 
-def end_to_end(F, w, ctx, stream, seed, args, world):
-    """The same step through the C ABI with host buffers: every step copies
-    the lattice in from pinned host memory, runs, computes the observables
-    and copies the lattice out."""
+def end_to_end(F, w, ctx, stream, seed, args, world, hnp):
+    """The same steps through the C ABI with host buffers, from the lattice
+    the timed steps started from (hnp, pinned host memory; a lattice that
+    relaxes has fewer events later on): every step copies the lattice in,
+    runs, computes the observables and copies the lattice out."""
     import torch
     lx, ly = w["lx"], w["ly"]
-    host = torch.empty(lx * ly, dtype=torch.uint8, pin_memory=True)
-    hnp = host.numpy()
-    ctx.get_state(0, hnp)
-    torch.cuda.synchronize()
     e0 = ctx.stats()["events"]
     step_t = STEP_WINDOWS_DT * w["dt"]
     barrier(world)
@@ -498,13 +499,14 @@ def run_workload(args, rank, world, local):
     if not args.no_variants:
         forms += [f for f in FORMS if f not in forms]
     res = {}
+    snap = torch.empty(w["lx"] * w["ly"], dtype=torch.uint8, pin_memory=True).numpy()
     with ClockSampler(local) as clk:
         for f in forms:
-            res[f] = time_form(F, w, f, stream, seed, args, flush, world)
+            res[f] = time_form(F, w, f, stream, seed, args, flush, world, snapshot=snap if f == args.form else None)
             if f != args.form:
                 res[f]["ctx"].close()
     head = res[args.form]
-    e2e = end_to_end(F, w, head["ctx"], stream, seed, args, world)
+    e2e = end_to_end(F, w, head["ctx"], stream, seed, args, world, snap)
     info = head["info"]
     head["ctx"].close()
     if rank != 0:
