@@ -37,9 +37,10 @@ __device__ __forceinline__ void zgbq_count(unsigned long long *counters, int lan
 }
 
 // Held to 64 registers (as the other one-window kernels) with four cells
-// per warp, to 80 with eight, where 64 would spill.
+// per warp, to 72 with eight (a small spill; 28 warps per SM with two-warp
+// blocks: faster than 80 registers without the spill, or 64 with more).
 template <int RL>
-__global__ void __launch_bounds__(RL == 8 ? 256 : 512, RL == 8 ? 3 : 2) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
+__global__ void __maxnreg__(RL == 8 ? 72 : 64) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
     constexpr int W = 32 / RL;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -70,10 +71,10 @@ __global__ void __launch_bounds__(RL == 8 ? 256 : 512, RL == 8 ? 3 : 2) fs_zgbq_
     zgbq_count<W>(a.counters, lane, valid, e, bad);
 }
 
-// Held to 64 registers (four 256-thread blocks per SM) with four cells per
-// warp, to 80 (three) with eight, where 64 would spill.
+// Held to 64 registers with four cells per warp, to 72 with eight (as the
+// one-window kernel).
 template <int RL>
-__global__ void __launch_bounds__(256, RL == 8 ? 3 : 4) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
+__global__ void __maxnreg__(RL == 8 ? 72 : 64) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
                                                                     int smem_per_warp)
 {
     constexpr int W = 32 / RL;
