@@ -283,6 +283,26 @@ fskmc_status fskmc_get_state(fskmc_ctx *ctx, int32_t replica, uint8_t *dst,
                              int32_t is_device);
 
 /*
+ * All replicas' lattices in one copy each way (a batch of M independent
+ * realisations, Section 7, moved between host and device without a call
+ * per replica). The state buffer holds the replicas back to back in order,
+ * replica r's lx*ly bytes (row-major states) from byte offset out[r], each
+ * offset a multiple of 256; out[replicas] is the buffer's size in bytes.
+ * The bytes between replicas are copied and otherwise unused; they must
+ * hold a state of the model like every other byte (0 will do).
+ * fskmc_state_layout: out has room for replicas + 1 entries; EINVAL: NULL.
+ * fskmc_set_state_all / fskmc_get_state_all: src / dst is a buffer of that
+ * size, device memory if is_device != 0. EINVAL: NULL buffer, a bit-packed
+ * context (use the per-replica calls), or (set) a byte that is not a state
+ * of the model, in which case every lattice is left cleared to 0. get with
+ * host memory waits for the copy; with device memory it is only queued on
+ * the context's stream.
+ */
+fskmc_status fskmc_state_layout(const fskmc_ctx *ctx, int64_t *out);
+fskmc_status fskmc_set_state_all(fskmc_ctx *ctx, const uint8_t *src, int32_t is_device);
+fskmc_status fskmc_get_state_all(fskmc_ctx *ctx, uint8_t *dst, int32_t is_device);
+
+/*
  * Advance every replica by physical time T with fractional windows of
  * length dt under the given schedule (Section 3). The window counter
  * continues across calls, so two runs of T/2 equal one run of T. T/dt must

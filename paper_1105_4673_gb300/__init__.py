@@ -34,7 +34,8 @@ EXPORTS = [
     "fskmc_create", "fskmc_batch_create", "fskmc_destroy", "fskmc_last_error",
     "fskmc_set_replica_id", "fskmc_set_clock", "fskmc_set_engine", "fskmc_set_warps_per_block",
     "fskmc_set_cell_grouping", "fskmc_set_edge_screen", "fskmc_set_spin_limit", "fskmc_set_task_order", "fskmc_info", "fskmc_init_random", "fskmc_init_bump",
-    "fskmc_set_state", "fskmc_get_state", "fskmc_run", "fskmc_window", "fskmc_get_window_index",
+    "fskmc_set_state", "fskmc_get_state", "fskmc_state_layout", "fskmc_set_state_all", "fskmc_get_state_all",
+    "fskmc_run", "fskmc_window", "fskmc_get_window_index",
     "fskmc_set_window_index", "fskmc_observables", "fskmc_stats", "fskmc_exact_edge_checks", "fskmc_workload", "fskmc_sync",
     "fskmc_observables_noalloc", "fskmc_autotune", "fskmc_selftest_divide", "fskmc_selftest_log",
     "fskmc_schedule", "fskmc_set_nesting",
@@ -95,6 +96,9 @@ def lib():
             "fskmc_init_bump": ([vp, C.c_uint64, C.c_double, C.c_double, C.c_int32], C.c_int),
             "fskmc_set_state": ([vp, C.c_int32, vp, C.c_int32], C.c_int),
             "fskmc_get_state": ([vp, C.c_int32, vp, C.c_int32], C.c_int),
+            "fskmc_state_layout": ([vp, C.POINTER(C.c_int64)], C.c_int),
+            "fskmc_set_state_all": ([vp, vp, C.c_int32], C.c_int),
+            "fskmc_get_state_all": ([vp, vp, C.c_int32], C.c_int),
             "fskmc_run": ([vp, C.c_int, C.c_double, C.c_double, C.c_uint64], C.c_int),
             "fskmc_window": ([vp, C.c_int32, C.c_double, C.c_uint64], C.c_int),
             "fskmc_get_window_index": ([vp, C.POINTER(C.c_uint64)], C.c_int),
@@ -263,6 +267,29 @@ class Context:
             out = np.empty(lx * ly, np.uint8)
         p, dev = _ptr_of(out)
         _check(lib().fskmc_get_state(self.h, replica, p, dev), self.h)
+        return out
+
+    def state_layout(self) -> np.ndarray:
+        """Byte offset of every replica's lattice in the batch's state buffer,
+        then the buffer's size (fskmc_state_layout)."""
+        out = (C.c_int64 * (len(self.sizes) + 1))()
+        _check(lib().fskmc_state_layout(self.h, out), self.h)
+        return np.array(out[:], np.int64)
+
+    def set_state_all(self, buf):
+        """Every replica's lattice in one copy, from a buffer in the layout of
+        state_layout() (host array, or a CUDA tensor)."""
+        if isinstance(buf, np.ndarray):
+            buf = np.ascontiguousarray(buf, dtype=np.uint8).reshape(-1)
+        p, dev = _ptr_of(buf)
+        _check(lib().fskmc_set_state_all(self.h, p, dev), self.h)
+
+    def get_state_all(self, out=None):
+        """Every replica's lattice in one copy, in the layout of state_layout()."""
+        if out is None:
+            out = np.empty(int(self.state_layout()[-1]), np.uint8)
+        p, dev = _ptr_of(out)
+        _check(lib().fskmc_get_state_all(self.h, p, dev), self.h)
         return out
 
     # -- the method --------------------------------------------------------

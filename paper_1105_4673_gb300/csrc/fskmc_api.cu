@@ -871,6 +871,47 @@ fskmc_status fskmc_get_state(fskmc_ctx *c, int32_t replica, uint8_t *dst, int32_
     return FSKMC_OK;
 }
 
+fskmc_status fskmc_state_layout(const fskmc_ctx *c, int64_t *out)
+{
+    if (!c || !out) return FSKMC_EINVAL;
+    for (int r = 0; r < c->nrep; ++r) out[r] = c->reps[r].lat_off;
+    out[c->nrep] = c->total_sites;
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_set_state_all(fskmc_ctx *c, const uint8_t *src, int32_t is_device)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (!src) return fail(c, FSKMC_EINVAL, "NULL src");
+    if (c->packed) return fail(c, FSKMC_EINVAL, "a bit-packed context takes its states one replica at a time");
+    // the byte lattices are laid out as the state buffer: one copy, one check
+    uint8_t *dst = c->d_lat[c->cur];
+    const int64_t n = c->total_sites;
+    CK(c, cudaMemcpyAsync(dst, src, (size_t)n, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaMemsetAsync(c->d_scratch_u32, 0, sizeof(unsigned int), c->stream));
+    CK(c, fskmc::launch_validate(dst, n, c->nstates, c->d_scratch_u32, c->stream));
+    unsigned int bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, c->d_scratch_u32, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (bad) {
+        CK(c, cudaMemsetAsync(dst, 0, (size_t)n, c->stream));
+        return fail(c, FSKMC_EINVAL, "%u bytes hold a value that is not a state of the model", bad);
+    }
+    return FSKMC_OK;
+}
+
+fskmc_status fskmc_get_state_all(fskmc_ctx *c, uint8_t *dst, int32_t is_device)
+{
+    if (!c) return FSKMC_EINVAL;
+    if (!dst) return fail(c, FSKMC_EINVAL, "NULL dst");
+    if (c->packed) return fail(c, FSKMC_EINVAL, "a bit-packed context gives its states one replica at a time");
+    CK(c, cudaMemcpyAsync(dst, c->d_lat[c->cur], (size_t)c->total_sites,
+                          is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!is_device) CK(c, cudaStreamSynchronize(c->stream));
+    return FSKMC_OK;
+}
+
 fskmc_status fskmc_run(fskmc_ctx *c, fskmc_scheme scheme, double dt, double T, uint64_t seed)
 {
     if (!c) return FSKMC_EINVAL;
