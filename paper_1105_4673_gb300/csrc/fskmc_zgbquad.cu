@@ -1,7 +1,6 @@
-// Kernels of the RL-cells-per-warp ZGB window (RL = 4: fskmc_zgb32x4.cuh,
-// rows in registers; RL = 8: fskmc_zgb32s.cuh, rows in shared memory):
-// 32-wide cells whose rows are a multiple of RL, from 2 RL to 32, with the
-// binary32 clock.
+// Kernels of the RL-cells-per-warp ZGB window (fskmc_zgb32x4.cuh; RL = 4 or
+// 8): 32-wide cells whose rows are a multiple of RL, from 2 RL to 32, with
+// the binary32 clock.
 //
 // fs_zgbq_window_kernel<RL>: one fractional window (Eqs. totalrate and
 // skeleton on every active cell), warp g running the window's active cells
@@ -16,7 +15,6 @@
 
 #include "fskmc_device.cuh"
 #include "fskmc_internal.h"
-#include "fskmc_zgb32s.cuh"
 #include "fskmc_zgb32x4.cuh"
 #include "philox.cuh"
 
@@ -38,12 +36,11 @@ __device__ __forceinline__ void zgbq_count(unsigned long long *counters, int lan
     }
 }
 
-// Held to 64 registers (32 warps per SM with two-warp blocks). With eight
-// cells per warp the window keeps its rows in shared memory
-// (fskmc_zgb32s.cuh), which leaves a small spill at 64 registers but runs
-// faster than 72 or 56.
+// Held to 64 registers (as the other one-window kernels) with four cells
+// per warp, to 72 with eight (a small spill; 28 warps per SM with two-warp
+// blocks: faster than 80 registers without the spill, or 64 with more).
 template <int RL>
-__global__ void __maxnreg__(64) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
+__global__ void __maxnreg__(RL == 8 ? 72 : 64) fs_zgbq_window_kernel(WindowArgs a, int nactive, int smem_per_warp)
 {
     constexpr int W = 32 / RL;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -67,22 +64,17 @@ __global__ void __maxnreg__(64) fs_zgbq_window_kernel(WindowArgs a, int nactive,
         }
     }
     bool bad = false;
-    uint32_t e;
-    if constexpr (RL == 8)
-        e = zgbs_window<RL, false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cell_at(R, a.geom, cx, cy),
-                                   valid, a.colour, a.w, a.h, a.seed, a.src + R.lat_off, a.dst + R.lat_off, lane,
-                                   &bad);
-    else
-        e = zgbm_window<RL, false>(smem + (size_t)wib * smem_per_warp, R, a.geom, cell_at(R, a.geom, cx, cy),
-                                   valid, a.colour, a.w, a.h, a.seed, a.src + R.lat_off, a.dst + R.lat_off, lane,
-                                   &bad);
+    const uint32_t e = zgbm_window<RL, false>(smem + (size_t)wib * smem_per_warp, R, a.geom,
+                                              cell_at(R, a.geom, cx, cy), valid, a.colour, a.w, a.h, a.seed,
+                                              a.src + R.lat_off, a.dst + R.lat_off, lane, &bad);
     if ((lane & (W - 1)) == 0 && valid) a.workload[R.cell_off + cy * R.ncx + cx] = (int32_t)e;
     zgbq_count<W>(a.counters, lane, valid, e, bad);
 }
 
-// Held to 64 registers (as the one-window kernel).
+// Held to 64 registers with four cells per warp, to 72 with eight (as the
+// one-window kernel).
 template <int RL>
-__global__ void __maxnreg__(64) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
+__global__ void __maxnreg__(RL == 8 ? 72 : 64) fs_zgbq_persistent_kernel(const __grid_constant__ PParams P,
                                                                     int smem_per_warp)
 {
     constexpr int W = 32 / RL;
@@ -149,13 +141,9 @@ __global__ void __maxnreg__(64) fs_zgbq_persistent_kernel(const __grid_constant_
             if (!ok) break;
         }
         bool bad = false;
-        uint32_t e;
-        if constexpr (RL == 8)
-            e = zgbs_window<RL, true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), valid, ccol, P.w0 + (uint32_t)i,
-                                      P.h[i], P.seed, P.lat + R.lat_off, P.lat + R.lat_off, lane, &bad);
-        else
-            e = zgbm_window<RL, true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), valid, ccol, P.w0 + (uint32_t)i,
-                                      P.h[i], P.seed, P.lat + R.lat_off, P.lat + R.lat_off, lane, &bad);
+        const uint32_t e = zgbm_window<RL, true>(wsm, R, P.geom, cell_at(R, P.geom, cx, cy), valid, ccol,
+                                                 P.w0 + (uint32_t)i, P.h[i], P.seed, P.lat + R.lat_off,
+                                                 P.lat + R.lat_off, lane, &bad);
         if (gl == 0 && valid) P.workload[slot] = (int32_t)e;
         zgbq_count<W>(P.counters, lane, valid, e, bad);
         // the warp barrier orders every lane's writes before the release
@@ -173,7 +161,7 @@ __global__ void __maxnreg__(64) fs_zgbq_persistent_kernel(const __grid_constant_
 
 size_t zgb_multi_smem_per_warp(int rl)
 {
-    return (size_t)(rl == 8 ? zgbs_warp_smem(8) : zgbm_warp_smem(rl));
+    return (size_t)zgbm_warp_smem(rl);
 }
 
 bool zgb_multi_shape(int rl, int qx, int qy)
